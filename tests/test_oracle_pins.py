@@ -1,0 +1,425 @@
+"""Pins of the float64 oracle against facts that do not come from the oracle:
+a hand-worked iteration, published generator vectors, library routines,
+closed forms, invariants of Eq. 2-4 and brute-force optima."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+from oracle import ap, lap, pap, rng
+
+
+def _load(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as f:
+        return json.load(f)
+
+
+def _rand_S(n, seed, ties=False, asym=True):
+    g = np.random.default_rng(seed)
+    if ties:
+        S = -g.integers(0, 6, size=(n, n)).astype(np.float64)
+    else:
+        S = -g.random((n, n)) * 10
+    if not asym:
+        S = 0.5 * (S + S.T)
+    np.fill_diagonal(S, np.median(S[~np.eye(n, dtype=bool)]))
+    return S
+
+
+def _separated(n_per=3, n_clusters=3, seed=0, sep=30.0, spread=1.0, d=2):
+    g = np.random.default_rng(seed)
+    centres = g.normal(size=(n_clusters, d)) * sep
+    X = np.concatenate([c + g.normal(size=(n_per, d)) * spread for c in centres])
+    return X, np.repeat(np.arange(n_clusters), n_per)
+
+
+# --- generator ----------------------------------------------------------------
+
+def test_splitmix64_published_vectors(golden_dir):
+    g = _load(golden_dir, "splitmix64_vectors.json")
+    got = [rng.output(g["seed"], n) for n in range(1, 6)]
+    assert got == [int(v) for v in g["outputs"]]
+    vec = rng.outputs(g["seed"], np.arange(1, 6, dtype=np.uint64))
+    assert [int(v) for v in vec] == [int(v) for v in g["outputs"]]
+
+
+def test_unit_interval_range():
+    u = rng.unit_interval(7, np.arange(1, 100001, dtype=np.uint64))
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.01
+
+
+# --- one iteration worked by hand (Eq. 2, 3, 4) ---------------------------------
+
+@pytest.mark.parametrize("literal", [True, False])
+def test_hand_example_one_iteration(golden_dir, literal):
+    g = _load(golden_dir, "ap_three_points_by_hand.json")
+    S = np.array(g["S"], dtype=np.float64)
+    Z = np.zeros((3, 3))
+    R, A = ap.iterate_once(S, Z, Z, 0.0, literal=literal)
+    assert np.array_equal(R, np.array(g["R"], dtype=np.float64))
+    assert np.array_equal(A, np.array(g["A"], dtype=np.float64))
+    assert list(ap.decisions(R, A)) == g["decisions"]
+    ex = ap.exemplars(S, R, A)
+    assert list(ex["idx"]) == g["idx"]
+    assert (ex["dpsim"], ex["expref"], ex["netsim"]) == (g["dpsim"], g["expref"], g["netsim"])
+
+
+def test_hand_example_damping_order(golden_dir):
+    g = _load(golden_dir, "ap_three_points_by_hand.json")
+    S = np.array(g["S"], dtype=np.float64)
+    Z = np.zeros((3, 3))
+    R, A = ap.iterate_once(S, Z, Z, 0.5)
+    assert np.array_equal(R, np.array(g["R"]) / 2.0)
+    assert np.array_equal(A, np.array(g["A"]) / 4.0)
+
+
+# --- the two statements of Eq. 2-4 agree ---------------------------------------
+
+@pytest.mark.parametrize("n,ties,seed", [(7, True, 1), (12, False, 2), (20, True, 3), (25, False, 4)])
+def test_literal_equals_top2_form(n, ties, seed):
+    S = _rand_S(n, seed, ties=ties)
+    a = ap.run(S, lam=0.5, fixed_iters=6, literal=True)
+    b = ap.run(S, lam=0.5, fixed_iters=6, literal=False)
+    scale = np.abs(S).max()
+    assert np.abs(a["R"] - b["R"]).max() <= 1e-12 * scale
+    assert np.abs(a["A"] - b["A"]).max() <= 1e-12 * scale
+
+
+def test_literal_equals_top2_form_nonzero_start():
+    S = _rand_S(15, 9)
+    g = np.random.default_rng(3)
+    R0 = g.normal(size=S.shape)
+    A0 = -np.abs(g.normal(size=S.shape))
+    a = ap.run(S, lam=0.7, fixed_iters=3, literal=True, R0=R0, A0=A0)
+    b = ap.run(S, lam=0.7, fixed_iters=3, literal=False, R0=R0, A0=A0)
+    assert np.abs(a["R"] - b["R"]).max() <= 1e-12 * 10
+    assert np.abs(a["A"] - b["A"]).max() <= 1e-12 * 10
+
+
+# --- invariants -----------------------------------------------------------------
+
+def test_availability_signs_every_iteration():
+    S = _rand_S(40, 5)
+    n = S.shape[0]
+    R = np.zeros_like(S)
+    A = np.zeros_like(S)
+    off = ~np.eye(n, dtype=bool)
+    for _ in range(30):
+        R, A = ap.iterate_once(S, R, A, 0.5)
+        assert (A[off] <= 0).all()
+        assert (np.diag(A) >= 0).all()
+
+
+def test_responsibility_undamped_row_structure():
+    S = _rand_S(30, 6)
+    A = -np.abs(np.random.default_rng(1).normal(size=S.shape))
+    Rn = ap.responsibility(S, A)
+    m1, j1, m2 = ap.row_top2(A + S)
+    T = A + Rn
+    n = S.shape[0]
+    assert np.allclose(T[np.arange(n), j1], m1 - m2, rtol=0, atol=1e-12)
+    assert (T[np.arange(n), j1] >= 0).all()
+    mask = np.ones_like(T, dtype=bool)
+    mask[np.arange(n), j1] = False
+    assert (T[mask] <= 1e-12).all()
+
+
+def test_positive_scaling():
+    S = _rand_S(30, 7)
+    a = ap.run(S, lam=0.5, fixed_iters=12)
+    b = ap.run(3.0 * S, lam=0.5, fixed_iters=12)
+    assert np.allclose(b["R"], 3.0 * a["R"], rtol=0, atol=1e-10)
+    assert np.allclose(b["A"], 3.0 * a["A"], rtol=0, atol=1e-10)
+    assert np.array_equal(ap.exemplar_mask(a["R"], a["A"]), ap.exemplar_mask(b["R"], b["A"]))
+
+
+def test_row_shift_invariance():
+    S = _rand_S(30, 8)
+    c = np.random.default_rng(2).normal(size=(30, 1)) * 5
+    a = ap.run(S, lam=0.5, fixed_iters=12)
+    b = ap.run(S + c, lam=0.5, fixed_iters=12)
+    assert np.allclose(a["R"], b["R"], atol=1e-10)
+    assert np.allclose(a["A"], b["A"], atol=1e-10)
+
+
+def test_permutation_equivariance():
+    S = _rand_S(30, 9)
+    p = np.random.default_rng(4).permutation(30)
+    a = ap.run(S, lam=0.5, fixed_iters=12)
+    b = ap.run(S[np.ix_(p, p)], lam=0.5, fixed_iters=12)
+    assert np.allclose(b["R"], a["R"][np.ix_(p, p)], atol=1e-12)
+    assert np.allclose(b["A"], a["A"][np.ix_(p, p)], atol=1e-12)
+
+
+# --- convergence, fixed point, outputs ----------------------------------------------
+
+def _separated_S(seed=0, n_per=4, n_clusters=3):
+    X, lab = _separated(n_per=n_per, n_clusters=n_clusters, seed=seed)
+    S, p = ap.build_similarity(X)
+    return X, lab, S
+
+
+def test_fixed_point_after_convergence():
+    _, _, S = _separated_S(1, n_per=8, n_clusters=4)
+    res = ap.run(S, lam=0.5, max_iter=2000, convits=2000)
+    dr, da = ap.undamped_residuals(S, res["R"], res["A"])
+    scale = np.abs(S).max()
+    assert dr <= 1e-6 * scale and da <= 1e-6 * scale
+
+
+def test_termination_rule():
+    _, _, S = _separated_S(2, n_per=6)
+    res = ap.run(S, lam=0.5, max_iter=200, convits=15)
+    assert res["converged"] and res["iters"] >= 15
+    masks = []
+    R = np.zeros_like(S)
+    A = np.zeros_like(S)
+    for _ in range(res["iters"]):
+        R, A = ap.iterate_once(S, R, A, 0.5)
+        masks.append(ap.exemplar_mask(R, A))
+    last = masks[-15:]
+    assert all(np.array_equal(m, last[0]) for m in last) and last[0].any()
+    # one iteration earlier the rule did not yet hold
+    prev = masks[-16:-1]
+    assert not (all(np.array_equal(m, prev[0]) for m in prev) and prev[0].any())
+    assert np.array_equal(R, res["R"]) and np.array_equal(A, res["A"])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_brute_force_optimum_small(seed):
+    _, _, S = _separated_S(seed, n_per=3, n_clusters=3)
+    res = ap.run(S, lam=0.5, max_iter=500, convits=30)
+    ex = ap.exemplars(S, res["R"], res["A"])
+    bestE, best = ap.brute_force_best(S)
+    assert np.array_equal(ex["E"], bestE)
+    assert abs(ex["netsim"] - best) <= 1e-9 * abs(best)
+
+
+def test_exemplar_self_consistency_and_energy():
+    X, lab, S = _separated_S(5, n_per=10, n_clusters=5)
+    res = ap.run(S, lam=0.5)
+    ex = ap.exemplars(S, res["R"], res["A"])
+    E = ex["E"]
+    idx = ex["idx"]
+    assert E.size > 0
+    assert np.array_equal(idx[E], E)
+    nonex = np.setdiff1d(np.arange(S.shape[0]), E)
+    assert np.isin(idx[nonex], E).all()
+    assert np.allclose(S[nonex, idx[nonex]], S[np.ix_(nonex, E)].max(axis=1))
+    # netsim = -E(c) with s(k,k) = p for exemplars (energy of Section 2)
+    energy = -sum(S[i, idx[i]] for i in range(S.shape[0]))
+    assert abs(ex["netsim"] - (-energy)) <= 1e-9 * abs(energy)
+    assert abs(ex["netsim"] - ap.netsim_of_labels(S, idx)) <= 1e-9 * abs(energy)
+    # separated clusters: one exemplar per true cluster
+    assert len(set(lab[E])) == 5 and E.size == 5
+
+
+def test_no_exemplar_output():
+    S = np.array([[-100.0, -1.0], [-1.0, -100.0]])
+    R = np.zeros((2, 2))
+    A = np.array([[-5.0, 0.0], [0.0, -5.0]])   # a+r picks the other point
+    ex = ap.exemplars(S, R, A)
+    assert (ex["idx"] == -1).all() and np.isnan(ex["netsim"])
+
+
+# --- similarity, preference, noise --------------------------------------------------
+
+def test_similarity_closed_form_line():
+    x = np.array([[0.0], [1.0], [3.0], [-2.0]])
+    S = ap.similarity(x)
+    want = -np.array([[(a - b) ** 2 for b in x[:, 0]] for a in x[:, 0]])
+    assert np.array_equal(S, want)
+
+
+def test_similarity_vs_scipy():
+    X = np.random.default_rng(0).normal(size=(50, 7)).astype(np.float32)
+    assert np.allclose(ap.similarity(X), -cdist(X.astype(np.float64), X.astype(np.float64), "sqeuclidean"),
+                       rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3, 10, 11])
+def test_offdiag_median_vs_numpy(n):
+    S = np.random.default_rng(n).normal(size=(n, n))
+    off = S[~np.eye(n, dtype=bool)]
+    assert ap.offdiag_median(S) == float(np.median(off))
+
+
+def test_offdiag_median_by_hand():
+    S = np.array([[9.0, 1.0, 2.0], [3.0, 9.0, 4.0], [5.0, 6.0, 9.0]])
+    assert ap.offdiag_median(S) == 3.5          # values 1..6: mean of 3 and 4
+
+
+def test_tiebreak_noise_magnitude():
+    X, _ = _separated(n_per=5, seed=1)
+    S0, p = ap.build_similarity(X)
+    S1, _ = ap.build_similarity(X, noise_rel=1e-6, seed=11)
+    d = S1 - S0
+    assert (d >= 0).all()                          # rel*|s|*u is never negative
+    assert (np.abs(d) <= 1e-6 * np.abs(S0) + 1e-300).all()
+    u = ap.tiebreak_noise(S0.shape[0], S0.shape[1], 11)
+    # S1 - S0 cancels: compare to within a few ulps of S0
+    assert (np.abs(d - 1e-6 * np.abs(S0) * u) <= 4 * np.finfo(float).eps * np.abs(S0)).all()
+    assert u[0, 0] == rng.unit_interval(11, np.array([1], dtype=np.uint64))[0]
+
+
+# --- Algorithm 2 (PAP) -------------------------------------------------------------
+
+@pytest.mark.parametrize("n,k", [(100, 4), (1000, 4), (2021, 16), (7, 3), (10, 1)])
+def test_equal_partition_rule(n, k):
+    off = pap.equal_partition(n, k)
+    sizes = np.diff(off)
+    m = n // k
+    assert len(sizes) == k and off[0] == 0 and off[-1] == n
+    assert (sizes[:-1] == m).all() and sizes[-1] == n - m * (k - 1)
+
+
+def test_block_count_bound():
+    assert pap.block_count_bound_ok(2021, 4, 86) is True      # 4 < 2021/344
+    assert pap.block_count_bound_ok(2021, 8, 86) is False     # Table 2's k=8 lies outside
+    assert pap.block_count_bound_ok(60000, 32, 50) is True
+    assert pap.block_count_bound_ok(60000, 1, 50) is False
+
+
+def test_merge_is_block_diagonal():
+    off = np.array([0, 2, 5, 6])
+    blocks = [np.full((2, 2), 1.0), np.full((3, 3), 2.0), np.full((1, 1), 3.0)]
+    Ap = pap.merge_blocks(6, off, blocks)
+    want = np.zeros((6, 6))
+    want[0:2, 0:2] = 1
+    want[2:5, 2:5] = 2
+    want[5, 5] = 3
+    assert np.array_equal(Ap, want)
+
+
+def test_pap_step4_from_zero_is_plain_ap():
+    _, _, S = _separated_S(3, n_per=6, n_clusters=4)
+    a = ap.run(S, lam=0.5)
+    b = ap.run(S, lam=0.5, R0=np.zeros_like(S), A0=pap.merge_blocks(S.shape[0], [0, S.shape[0]],
+                                                                      [np.zeros_like(S)]))
+    assert np.array_equal(a["R"], b["R"]) and a["iters"] == b["iters"]
+
+
+def test_pap_single_block_subrun_is_plain_ap():
+    _, _, S = _separated_S(4, n_per=5, n_clusters=3)
+    r = pap.run(S, [0, S.shape[0]], lam=0.5)
+    a = ap.run(S, lam=0.5)
+    assert np.array_equal(r["sub"][0]["A"], a["A"])
+
+
+def test_pap_netsim_close_to_ap():
+    g = np.random.default_rng(11)
+    centres = g.uniform(-10, 10, size=(5, 2))
+    X = np.concatenate([c + g.normal(size=(40, 2)) for c in centres])
+    X = X[g.permutation(len(X))]
+    S, _ = ap.build_similarity(X)
+    a = ap.run(S, lam=0.5, max_iter=500)
+    ea = ap.exemplars(S, a["R"], a["A"])
+    r = pap.run(S, pap.equal_partition(S.shape[0], 4), lam=0.5, max_iter=500)
+    er = ap.exemplars(S, r["final"]["R"], r["final"]["A"])
+    # Section 3: the result is "similar to or even better than" plain AP
+    assert er["netsim"] >= ea["netsim"] * (1 + 0.005)
+
+
+# --- Algorithm 3 (LAP) -------------------------------------------------------------
+
+def test_uniform_landmarks():
+    lm = lap.uniform_landmarks(1000, 100, 5)
+    assert lm.size == 100 and np.unique(lm).size == 100
+    assert (np.diff(lm) > 0).all() and lm.max() < 1000
+    assert np.array_equal(lm, lap.uniform_landmarks(1000, 100, 5))
+    assert not np.array_equal(lm, lap.uniform_landmarks(1000, 100, 6))
+
+
+def test_lap_all_points_as_landmarks_is_ap():
+    X, _ = _separated(n_per=8, n_clusters=4, seed=7)
+    r = lap.run(X, np.arange(X.shape[0]), lam=0.5)
+    S, _ = ap.build_similarity(X)
+    a = ap.run(S, lam=0.5)
+    ea = ap.exemplars(S, a["R"], a["A"])
+    assert np.array_equal(r["E"], ea["E"])
+    assert np.array_equal(r["idx"], ea["idx"])
+    assert abs(r["netsim"] - ea["netsim"]) <= 1e-9 * abs(ea["netsim"])
+
+
+def test_lap_assignment_brute_force():
+    g = np.random.default_rng(3)
+    X = g.normal(size=(60, 3))
+    C = g.normal(size=(7, 3))
+    near = lap.nearest_exemplar(X, C)
+    for i in range(60):
+        d = [sum((X[i, j] - C[c, j]) ** 2 for j in range(3)) for c in range(7)]
+        assert near[i] == int(np.argmin(d))
+
+
+# --- the pins catch plausible mistakes planted in copies of the oracle ---------------
+
+def _mutant_iterations():
+    def rho_m1_everywhere(S, A):            # forgets the k == argmax case of Eq. 2
+        return S - (A + S).max(axis=1, keepdims=True)
+
+    def alpha_no_rkk(R):                     # drops r(k,k) in Eq. 3
+        colp, _ = ap.column_sums(R)
+        P = np.maximum(R, 0.0)
+        A = np.minimum(0.0, colp[None, :] - P)
+        np.fill_diagonal(A, colp)
+        return A
+
+    def alpha_transposed(R):                 # sums rows instead of columns
+        return ap.availability(R.T).T
+
+    def alpha_keeps_own_term(R):             # forgets to exclude i' = i in Eq. 3
+        colp, rkk = ap.column_sums(R)
+        A = np.minimum(0.0, rkk[None, :] + colp[None, :] + 0 * R)
+        np.fill_diagonal(A, colp)
+        return A
+
+    def alpha_diag_includes_self(R):         # Eq. 4 summed over all i'
+        A = ap.availability(R)
+        np.fill_diagonal(A, np.maximum(R, 0).sum(axis=0))
+        return A
+
+    def damp_a_first(S, R, A, lam):          # A from the undamped R
+        Rn = ap.responsibility(S, A)
+        An = ap.availability(Rn)
+        return lam * R + (1 - lam) * Rn, lam * A + (1 - lam) * An
+
+    def std(rho=ap.responsibility, alpha=ap.availability):
+        def it(S, R, A, lam):
+            R = lam * R + (1 - lam) * rho(S, A)
+            return R, lam * A + (1 - lam) * alpha(R)
+        return it
+
+    return {
+        "rho_m1_everywhere": std(rho=rho_m1_everywhere),
+        "alpha_no_rkk": std(alpha=alpha_no_rkk),
+        "alpha_transposed": std(alpha=alpha_transposed),
+        "alpha_keeps_own_term": std(alpha=alpha_keeps_own_term),
+        "alpha_diag_includes_self": std(alpha=alpha_diag_includes_self),
+        "damp_a_first": damp_a_first,
+    }
+
+
+@pytest.mark.parametrize("name", sorted(_mutant_iterations()))
+def test_hand_pins_catch_planted_mistake(golden_dir, name):
+    g = _load(golden_dir, "ap_three_points_by_hand.json")
+    S = np.array(g["S"], dtype=np.float64)
+    Z = np.zeros((3, 3))
+    it = _mutant_iterations()[name]
+    R0, A0 = it(S, Z, Z, 0.0)
+    R5, A5 = it(S, Z, Z, 0.5)
+    hand_ok = (np.array_equal(R0, np.array(g["R"], float)) and np.array_equal(A0, np.array(g["A"], float))
+               and np.array_equal(R5, np.array(g["R"]) / 2.0) and np.array_equal(A5, np.array(g["A"]) / 4.0))
+    # the literal statement of Eq. 2-4 is the second, independent pin
+    Sr = _rand_S(12, 21)
+    np.fill_diagonal(Sr, -0.01)      # high preferences: some r(k,k) > 0
+    lit = ap.run(Sr, lam=0.5, fixed_iters=6, literal=True)
+    R = np.zeros_like(Sr)
+    A = np.zeros_like(Sr)
+    for _ in range(6):
+        R, A = it(Sr, R, A, 0.5)
+    literal_ok = np.abs(R - lit["R"]).max() <= 1e-9 and np.abs(A - lit["A"]).max() <= 1e-9
+    assert not (hand_ok and literal_ok)
