@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark: dense affinity propagation on one GB300 through the C ABI.
+
+A step is one pass of the hot path over one synthetic problem: the similarity
+build (ap_similarity: centred GEMM + exact median preference), the damped
+sweep to convergence (ap_iterate) and the outputs (ap_exemplars).  Workload:
+N=20000 points in 64-D from a seeded mixture of 50 Gaussians (centres
+N(0,25 I), sigma 1, Dirichlet(2) weights), damping 0.9, at most 1000
+iterations, stop after 15 unchanged exemplar sets.
+
+value = algorithmic sweep bytes (20 B per matrix element per iteration: S, R,
+A read once, R, A written once) over the whole step's device time, in GB/s.
+Inputs stay resident in HBM; S, R, A are 1.6 GB each (> L2), so no L2 flush
+is needed between steps.  ``e2e`` repeats the step through the same C ABI
+with the features in pinned host memory and the labels copied back.
+
+--impl reference times the float64 CPU oracle on a bounded sample of the same
+workload (the oracle is the only reference: the paper ships no code).
+
+Multi-GPU: independent replicas (the method's sweep is not sharded here), one
+process per GPU under torchrun; value = all ranks' bytes / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS, DIM = 20000, 64
+DAMPING, MAX_ITER, CONV_ITER = 0.9, 1000, 15
+METRIC = "AP sweep HBM GB/s vs peak; time-to-converge vs plain GPU AP at equal net sim"
+WORKLOAD = ("plain dense AP, N=20000, d=64, 50-Gaussian mixture (centres N(0,25I), sigma 1, "
+            "Dirichlet(2) weights); S via BF16 tcgen05 GEMM + FP32 norms (or FP32 SIMT GEMM); "
+            "preference = off-diagonal median; damping 0.9, max 1000 iters, 15 unchanged sweeps")
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_0910_1650_gb300", "csrc", "sweep.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(n):
+    """ncu DRAM bytes per sweep launch, if the committed capture matches the
+    current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("source_hash") != _kernel_source_hash():
+        return None
+    per_elem = t["dram_bytes_per_launch"] / float(t["n"]) ** 2
+    return per_elem * n * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    capi.lib()
+
+    X, _ = synth.workload(1)
+    n, d = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    Xh = torch.from_numpy(X).pin_memory()
+    S = capi.empty_square(n, dev)
+    R = capi.empty_square(n, dev)
+    A = capi.empty_square(n, dev)
+    stream = torch.cuda.current_stream()
+
+    def step(X_in):
+        capi.ap_similarity(X_in, S, precision=args.precision)
+        R.zero_()
+        A.zero_()
+        _, _, res, _ = capi.ap_iterate(S, R, A, damping=DAMPING, max_iter=MAX_ITER,
+                                       conv_iter=CONV_ITER, time_sweep=True, decisions=False)
+        idx, ex = capi.ap_exemplars(S, R, A)
+        return res, ex, idx
+
+    for _ in range(args.warmup):
+        step(Xd)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region ------------------------------------------
+    launches0 = capi.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, sweep_ms, sweep_launches, results = 0, 0.0, 0, []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res, ex, _ = step(Xd)
+            iters += res["iters"]
+            sweep_ms += res["sweep_ms"]
+            sweep_launches += res["sweep_launches"]
+            results.append((res, ex))
+        ev1.record(stream)
+        barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = capi.kernel_launches() - launches0
+    bytes_done = 20.0 * n * n * iters
+    times = torch.tensor([elapsed], device=dev)
+    tot_bytes = torch.tensor([bytes_done], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot_bytes, op=dist.ReduceOp.SUM)
+    elapsed_max = float(times.item())
+    value = float(tot_bytes.item()) / elapsed_max / 1e9
+
+    # ---- end to end through the C ABI: host features in, labels out ------------
+    barrier()
+    e0 = time.perf_counter()
+    ev0.record(stream)
+    e_iters = 0
+    for _ in range(args.steps):
+        Xs = Xh.to(dev, non_blocking=True)
+        res, ex, idx = step(Xs)
+        lab = idx.to("cpu")
+        e_iters += res["iters"]
+    ev1.record(stream)
+    barrier()
+    e_elapsed = ev0.elapsed_time(ev1) / 1e3
+    e_wall = time.perf_counter() - e0
+    e_bytes = torch.tensor([20.0 * n * n * e_iters], device=dev, dtype=torch.float64)
+    e_t = torch.tensor([max(e_elapsed, 1e-9)], device=dev)
+    if world > 1:
+        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e_bytes, op=dist.ReduceOp.SUM)
+    e_value = float(e_bytes.item()) / float(e_t.item()) / 1e9
+
+    if rank == 0:
+        peaks, src = _peaks()
+        sweep_bytes_per_iter = 20.0 * n * n
+        # launch 1 has no availability half and the last launch no responsibility
+        # half; both move 16 B per element, the others 20 B
+        alg_bytes = n * n * (20.0 * max(sweep_launches - 2 * args.steps, 0) + 32.0 * args.steps)
+        achieved = alg_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+        traffic = _traffic(n)
+        last_res, last_ex = results[-1]
+        line = {
+            "metric": METRIC,
+            "value": round(value, 2),
+            "unit": "GB/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(elapsed_max / args.steps * 1e3, 3),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded generator; paper datasets unavailable)",
+            "config": {"workload": WORKLOAD, "n": n, "d": d, "precision": args.precision,
+                       "damping": DAMPING, "max_iter": MAX_ITER, "conv_iter": CONV_ITER,
+                       "iters_per_step": last_res["iters"],
+                       "n_exemplars": last_ex["n_exemplars"], "netsim": last_ex["netsim"],
+                       "l2": "inputs larger than L2 (S, R, A 1.6 GB each); no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"kernel": "sweep_kernel", "bound": "hbm",
+                         "achieved": round(achieved, 1) if achieved else None,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / peaks["hbm_gbs"], 4) if achieved else None,
+                         "traffic": traffic, "peak_source": src,
+                         "alg_bytes_per_launch": sweep_bytes_per_iter,
+                         "launch_ms": round(sweep_ms / max(sweep_launches, 1), 4)},
+            "e2e": {"value": round(e_value, 2), "unit": "GB/s",
+                    "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(n * 4 + 56),
+                    "wall_s": round(e_wall, 3)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(n_sample, seconds):
+    """The float64 oracle on the first n_sample points of the same workload:
+    S build, then iterations until ``seconds`` of iterating have passed."""
+    from oracle import ap as oap
+    from paper_0910_1650_gb300 import synth
+
+    X, _ = synth.workload(1)
+    Xs = X[:n_sample]
+    S, _ = oap.build_similarity(Xs)
+    R = np.zeros_like(S)
+    A = np.zeros_like(S)
+    t0 = time.perf_counter()
+    its = 0
+    while True:
+        R, A = oap.iterate_once(S, R, A, DAMPING)
+        its += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return its, dt
+
+
+def cpu_baseline(seconds):
+    n_sample = 3000
+    its, dt = _oracle_sample(n_sample, seconds)
+    gbs = 20.0 * n_sample * n_sample * its / dt / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"float64 oracle, first {n_sample} points of the N=20000 workload, "
+                      f"{its} iterations in {dt:.1f} s (numpy, one thread of "
+                      f"{len(os.sched_getaffinity(0))} host cores)"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    n_sample = 3000
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        _oracle_sample(n_sample, per_step / 4)
+    tot_its, tot_dt = 0, 0.0
+    for _ in range(args.steps):
+        its, dt = _oracle_sample(n_sample, per_step)
+        tot_its += its
+        tot_dt += dt
+    v = 20.0 * n_sample * n_sample * tot_its / tot_dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_POINTS, "d": DIM,
+                       "sample_points": n_sample},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"float64 oracle on the first {n_sample} points, "
+                                       f"{tot_its} iterations"},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * apgb.h -- C ABI of the GB300 affinity-propagation library (libapgb.so).
+ *
+ * Method: Xia, Wu, Zhang, Zhuang, "Local and global approaches of affinity
+ * propagation clustering for large scale data": Algorithm 1 (affinity
+ * propagation, Section 2, Eq. 1-4), Algorithm 2 (partition AP, Section 3) and
+ * Algorithm 3 (landmark AP, Section 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are row-major float32 with a leading dimension ``ld`` counted in
+ *    elements.  N x N matrices need ld >= N, ld % 4 == 0 and a 16-byte aligned
+ *    base pointer (128-bit row loads).  Columns N..ld-1 are never read as data
+ *    and never written.
+ *  - Every pointer documented "device" is caller-owned device memory; the
+ *    library allocates no device memory of its own.  Scratch comes from the
+ *    caller's workspace ``ws`` (device, 256-byte aligned, ``ws_bytes`` long),
+ *    whose size the matching *_workspace_size query returns.  The workspace
+ *    contents are not preserved between calls.
+ *  - ``stream`` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls whose output includes a host struct (ap_result*, a float*
+ *    documented "host") synchronise that stream before returning; the others
+ *    only enqueue work.
+ *  - Return value: 0 = AP_OK, > 0 = a warning with valid outputs, < 0 = an
+ *    error (outputs undefined).  No C++ exception crosses this boundary.
+ *  - Calls are not thread-safe with respect to one workspace.
+ */
+#ifndef APGB_H
+#define APGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AP_OK                 0
+#define AP_NOT_CONVERGED      1   /* max_iter reached; results are valid      */
+#define AP_NO_EXEMPLARS       2   /* no point chose itself; idx = -1          */
+#define AP_ERR_INVALID_ARG   -1   /* bad size, pointer, alignment or param    */
+#define AP_ERR_CUDA          -2   /* a CUDA runtime call failed               */
+#define AP_ERR_WORKSPACE     -3   /* ws is NULL, misaligned or too small      */
+#define AP_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up       */
+#define AP_ERR_NONFINITE     -5   /* S holds NaN or +-Inf                     */
+#define AP_ERR_UNSUPPORTED   -6   /* e.g. the GPU is not sm_103               */
+
+/* ---- options --------------------------------------------------------------- */
+#define AP_PREC_FP32   0   /* similarity by a float32 SIMT GEMM                  */
+#define AP_PREC_BF16   1   /* similarity by a bf16 tcgen05 GEMM, fp32 accumulate */
+
+#define AP_PREF_MEDIAN 0   /* p = median of the off-diagonal similarities        */
+#define AP_PREF_SCALAR 1   /* p = pref[0] for every point (pref: host float*)    */
+#define AP_PREF_VECTOR 2   /* p(k) = pref[k] (pref: device float[N])             */
+
+/* Parameters of Algorithm 1.  Section 2: each message is damped as
+ * lambda*old + (1-lambda)*new with 0.5 <= lambda < 1 (any value in [0,1) is
+ * accepted); Step 4 stops after a fixed number of iterations or once the
+ * decisions have been constant for some iterations. */
+typedef struct ap_params {
+    float   damping;      /* lambda in [0, 1)                                     */
+    int32_t max_iter;     /* >= 1                                                 */
+    int32_t conv_iter;    /* stop once the exemplar set is non-empty and has been
+                             identical for conv_iter consecutive iterations;
+                             0 = run exactly max_iter iterations                  */
+    int32_t check_every;  /* iterations enqueued between host checks of the
+                             device-side stop flag; 0 = automatic                 */
+    int32_t flags;        /* AP_FLAG_* bits                                       */
+} ap_params;
+
+/* ap_params.flags: bracket every sweep launch with CUDA events on the
+ * caller's stream and report their summed duration in ap_result.sweep_ms. */
+#define AP_FLAG_TIME_SWEEP 1
+
+/* Outputs of Algorithm 1 (Section 2): dpsim = sum of the data-point
+ * similarities to their exemplars, expref = sum of the exemplars'
+ * preferences, netsim = dpsim + expref (= -E(c) of the energy in Section 2). */
+typedef struct ap_result {
+    int32_t iters;        /* iterations whose messages are returned               */
+    int32_t converged;    /* 1 if the conv_iter rule stopped the run              */
+    int32_t n_exemplars;
+    int32_t status;       /* the call's return value, repeated                    */
+    double  dpsim, expref, netsim;
+    double  sweep_ms;     /* with AP_FLAG_TIME_SWEEP: summed sweep-kernel time    */
+    int32_t sweep_launches; /* sweep-kernel launches that did work               */
+    int32_t pad;
+} ap_result;
+
+/* ---------------------------------------------------------------------------
+ * ap_similarity -- s(i,k) = -||x_i - x_k||^2 (Section 2) and the preferences
+ * on the diagonal (Algorithm 1 input p(j)).
+ *
+ *  X        device float32 [n x ldx], row i = x_i (d features used).
+ *  S        device float32 [n x lds] output.
+ *  precision AP_PREC_FP32 or AP_PREC_BF16.  Both centre X on its mean first
+ *           (distances are translation invariant).  BF16 rounds the centred
+ *           features to bf16 and takes the squared norms of the rounded
+ *           vectors in fp32, so S is the fp32-accumulated negative squared
+ *           distance of the rounded points.  Off-diagonal values are clamped
+ *           to <= 0.
+ *  pref_mode AP_PREF_*; for AP_PREF_MEDIAN the median of the n(n-1)
+ *           off-diagonal entries (mean of the two middle order statistics,
+ *           formed in double and rounded to float, when n(n-1) is even).
+ *  noise_rel, seed  tie-break noise s <- s + noise_rel*|s|*u(i,k) applied to
+ *           every entry after the diagonal is set; u(i,k) in [0,1) is the top
+ *           53 bits of splitmix64 output number i*n+k+1 of ``seed``, times
+ *           2^-53.  noise_rel = 0 skips the pass.
+ *  pref_out host float* (may be NULL): receives the scalar preference used
+ *           (NaN for AP_PREF_VECTOR).  Non-NULL makes the call synchronous.
+ * ------------------------------------------------------------------------- */
+size_t    ap_similarity_workspace_size(int64_t n, int64_t d);
+int32_t   ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx,
+                        float* S, int64_t lds, int32_t precision,
+                        int32_t pref_mode, const float* pref,
+                        double noise_rel, uint64_t seed, float* pref_out,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ap_preference_median -- the preference used when the paper's experiments
+ * "adjust the input preference" to a common value (Section 5): the exact
+ * median of the n(n-1) off-diagonal entries of S (the diagonal is ignored;
+ * mean of the two middle order statistics in double, rounded to float, when
+ * n(n-1) is even).  Exact selection on the float32 bit patterns, 3 passes.
+ *
+ *  S        device float32 [n x ld], n >= 2.
+ *  median   host float* out (required); the call is synchronous.
+ * ------------------------------------------------------------------------- */
+size_t    ap_preference_median_workspace_size(int64_t n);
+int32_t   ap_preference_median(const float* S, int64_t n, int64_t ld, float* median,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ap_iterate -- the damped message-passing sweep of Algorithm 1:
+ *   Eq. 2  r(i,k) <- s(i,k) - max_{k'!=k} (a(i,k') + s(i,k'))
+ *   Eq. 3  a(i,k) <- min(0, r(k,k) + sum_{i' not in {i,k}} max(0, r(i',k)))
+ *   Eq. 4  a(k,k) <- sum_{i' != k} max(0, r(i',k))
+ * R is damped before A is formed from it.  Decisions (Section 2): point i
+ * picks the lowest k maximising a(i,k)+r(i,k); E = {k : pick(k) == k}.
+ *
+ *  S         device float32 [n x ld], preferences on the diagonal.
+ *  R, A      device float32 [n x ld], in/out: the initial messages on entry
+ *            (zeros for Eq. 1; A' for Algorithm 2 Step 4), the final ones on
+ *            return.
+ *  decisions device int32 [n] out (may be NULL): each point's pick after the
+ *            last iteration.
+ *  out       host ap_result* (may be NULL): iters, converged (dpsim/expref/
+ *            netsim are left 0; see ap_exemplars).  The call always
+ *            synchronises ``stream`` before returning.
+ *  Errors: AP_ERR_NONFINITE if S holds NaN/Inf (checked on the device first).
+ *  Returns AP_NOT_CONVERGED when conv_iter > 0 and max_iter was reached.
+ * ------------------------------------------------------------------------- */
+size_t    ap_iterate_workspace_size(int64_t n, int64_t ld);
+int32_t   ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
+                     const ap_params* params, int32_t* decisions,
+                     ap_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ap_exemplars -- outputs of Algorithm 1 from final messages.
+ * E = {k : argmax_j (a(k,j)+r(k,j)) == k} (lowest index on ties); exemplars
+ * keep idx(k) = k, every other point takes the exemplar of highest s(i,k)
+ * (lowest index on ties).  dpsim, expref and netsim are reduced in float64 in
+ * a fixed order (bitwise reproducible).
+ *
+ *  idx   device int32 [n] out; all -1 (and AP_NO_EXEMPLARS) when E is empty.
+ *  out   host ap_result* (required): n_exemplars, dpsim, expref, netsim.
+ * ------------------------------------------------------------------------- */
+size_t    ap_exemplars_workspace_size(int64_t n);
+int32_t   ap_exemplars(const float* S, const float* R, const float* A,
+                       int64_t n, int64_t ld, int32_t* idx, ap_result* out,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* ---- misc ------------------------------------------------------------------ */
+const char* ap_status_string(int32_t status);
+int32_t     ap_version(void);            /* major*10000 + minor*100 + patch   */
+/* Number of kernels this library has launched in this process (all devices,
+ * all threads); for accounting in benchmarks. */
+uint64_t    ap_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APGB_H */

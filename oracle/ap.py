@@ -176,14 +176,19 @@ def iterate_once(S, R, A, lam, literal=False):
     return R, A
 
 
-def decisions(R: np.ndarray, A: np.ndarray) -> np.ndarray:
-    """choice(i) = lowest k maximising a(i,k) + r(i,k)."""
-    return np.argmax(A + R, axis=1).astype(np.int64)
+def decisions(R: np.ndarray, A: np.ndarray, dtype=np.float64) -> np.ndarray:
+    """choice(i) = lowest k maximising a(i,k) + r(i,k).
+
+    ``dtype`` is the precision in which a+r is formed before the arg-max; a
+    comparison against a float32 implementation takes the decision in
+    float32 on both sides."""
+    T = np.asarray(A, dtype=dtype) + np.asarray(R, dtype=dtype)
+    return np.argmax(T, axis=1).astype(np.int64)
 
 
-def exemplar_mask(R, A) -> np.ndarray:
+def exemplar_mask(R, A, dtype=np.float64) -> np.ndarray:
     n = R.shape[0]
-    return decisions(R, A) == np.arange(n)
+    return decisions(R, A, dtype) == np.arange(n)
 
 
 def run(S, lam=0.5, max_iter=200, convits=15, R0=None, A0=None,
@@ -219,14 +224,15 @@ def run(S, lam=0.5, max_iter=200, convits=15, R0=None, A0=None,
     return dict(R=R, A=A, iters=t, converged=converged)
 
 
-def exemplars(S, R, A):
+def exemplars(S, R, A, dtype=np.float64):
     """Outputs of Algorithm 1: idx(j), dpsim, expref, netsim.
 
     Returns dict(idx int64[N] (-1 everywhere if there is no exemplar),
-    E (sorted exemplar indices), dpsim, expref, netsim)."""
+    E (sorted exemplar indices), dpsim, expref, netsim).  ``dtype`` as in
+    ``decisions``."""
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
-    E = np.nonzero(exemplar_mask(R, A))[0]
+    E = np.nonzero(exemplar_mask(R, A, dtype))[0]
     if E.size == 0:
         return dict(idx=np.full(n, -1, dtype=np.int64), E=E,
                     dpsim=np.nan, expref=np.nan, netsim=np.nan)

@@ -1,0 +1,224 @@
+"""Thin Python binding of libapgb.so (ctypes).
+
+Argument marshalling only: every step runs in the CUDA library.  Tensors are
+torch CUDA tensors (torch provides device memory and streams); the functions
+carry the names of the C entry points in ``include/apgb.h``.  If the library
+is missing or a call fails, an exception is raised -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libapgb.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "apgb.h")
+
+AP_OK = 0
+AP_NOT_CONVERGED = 1
+AP_NO_EXEMPLARS = 2
+AP_PREC_FP32, AP_PREC_BF16 = 0, 1
+AP_PREF_MEDIAN, AP_PREF_SCALAR, AP_PREF_VECTOR = 0, 1, 2
+AP_FLAG_TIME_SWEEP = 1
+
+
+class ApParams(C.Structure):
+    _fields_ = [("damping", C.c_float), ("max_iter", C.c_int32), ("conv_iter", C.c_int32),
+                ("check_every", C.c_int32), ("flags", C.c_int32)]
+
+
+class ApResult(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("n_exemplars", C.c_int32),
+                ("status", C.c_int32), ("dpsim", C.c_double), ("expref", C.c_double),
+                ("netsim", C.c_double), ("sweep_ms", C.c_double),
+                ("sweep_launches", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class ApgbError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} failed: {status} ({status_string(status)})")
+
+
+_lib = None
+_P = C.c_void_p
+_I64 = C.c_int64
+_SZ = C.c_size_t
+
+_SIGNATURES = {
+    "ap_similarity_workspace_size": (_SZ, [_I64, _I64]),
+    "ap_similarity": (C.c_int32, [_P, _I64, _I64, _I64, _P, _I64, C.c_int32, C.c_int32, _P,
+                                  C.c_double, C.c_uint64, _P, _P, _SZ, _P]),
+    "ap_preference_median_workspace_size": (_SZ, [_I64]),
+    "ap_preference_median": (C.c_int32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
+    "ap_iterate_workspace_size": (_SZ, [_I64, _I64]),
+    "ap_iterate": (C.c_int32, [_P, _P, _P, _I64, _I64, C.POINTER(ApParams), _P,
+                               C.POINTER(ApResult), _P, _SZ, _P]),
+    "ap_exemplars_workspace_size": (_SZ, [_I64]),
+    "ap_exemplars": (C.c_int32, [_P, _P, _P, _I64, _I64, _P, C.POINTER(ApResult), _P, _SZ, _P]),
+    "ap_status_string": (C.c_char_p, [C.c_int32]),
+    "ap_version": (C.c_int32, []),
+    "ap_kernel_launches": (C.c_uint64, []),
+}
+
+
+def header_functions():
+    """Names of every function declared in include/apgb.h."""
+    with open(HEADER) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(ap[a-z_0-9]*)\s*\(", text)))
+
+
+def lib():
+    """The loaded library (loads it on first use; raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU path)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().ap_status_string(int(s)).decode()
+
+
+def kernel_launches() -> int:
+    return int(lib().ap_kernel_launches())
+
+
+def _check(fn, status, ok=(AP_OK, AP_NOT_CONVERGED, AP_NO_EXEMPLARS)):
+    if status not in ok:
+        raise ApgbError(fn, status)
+    return status
+
+
+def _dev_f32(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D with unit column stride")
+    return t
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """Caller-owned scratch for one call (torch allocation, 256-B aligned)."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def padded_ld(n: int) -> int:
+    """Leading dimension used for library-allocated N x N matrices (x32)."""
+    return (n + 31) // 32 * 32
+
+
+def empty_square(n: int, device, fill=None) -> torch.Tensor:
+    """N x N float32 view with a 32-padded leading dimension."""
+    ld = padded_ld(n)
+    base = torch.empty((n, ld), dtype=torch.float32, device=device)
+    if fill is not None:
+        base.fill_(fill)
+    return base[:, :n]
+
+
+# ---------------------------------------------------------------------------
+
+def ap_similarity(X, S=None, precision="fp32", pref="median", noise_rel=0.0, seed=0,
+                  stream=None):
+    """S (n x n) from features X (n x d); returns (S, preference used)."""
+    _dev_f32(X, "X")
+    n, d = X.shape
+    if S is None:
+        S = empty_square(n, X.device)
+    _dev_f32(S, "S")
+    prec = {"fp32": AP_PREC_FP32, "bf16": AP_PREC_BF16}[precision]
+    keep = None
+    if isinstance(pref, str):
+        mode, pptr = AP_PREF_MEDIAN, None
+    elif isinstance(pref, torch.Tensor):
+        keep = pref.to(device=X.device, dtype=torch.float32).contiguous()
+        mode, pptr = AP_PREF_VECTOR, C.c_void_p(keep.data_ptr())
+    else:
+        keep = (C.c_float * 1)(float(pref))
+        mode, pptr = AP_PREF_SCALAR, C.cast(keep, C.c_void_p)
+    ws = workspace(lib().ap_similarity_workspace_size(n, d), X.device)
+    out = C.c_float(0.0)
+    st = lib().ap_similarity(C.c_void_p(X.data_ptr()), n, d, X.stride(0),
+                             C.c_void_p(S.data_ptr()), S.stride(0), prec, mode, pptr,
+                             float(noise_rel), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                             C.cast(C.pointer(out), C.c_void_p), C.c_void_p(ws.data_ptr()),
+                             ws.numel(), _stream(stream))
+    _check("ap_similarity", st, ok=(AP_OK,))
+    return S, float(out.value)
+
+
+def ap_preference_median(S, stream=None):
+    """Exact median of the off-diagonal entries of S (float)."""
+    _dev_f32(S, "S")
+    n = S.shape[0]
+    ws = workspace(lib().ap_preference_median_workspace_size(n), S.device)
+    out = C.c_float(0.0)
+    st = lib().ap_preference_median(C.c_void_p(S.data_ptr()), n, S.stride(0),
+                                    C.cast(C.pointer(out), C.c_void_p),
+                                    C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check("ap_preference_median", st, ok=(AP_OK,))
+    return float(out.value)
+
+
+def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check_every=0,
+               time_sweep=False, decisions=True, stream=None):
+    """Runs Algorithm 1 in place on (R, A) (zeros when omitted).
+    Returns (R, A, result dict, decisions int32 tensor or None)."""
+    _dev_f32(S, "S")
+    n = S.shape[0]
+    if R is None:
+        R = empty_square(n, S.device, 0.0)
+    if A is None:
+        A = empty_square(n, S.device, 0.0)
+    _dev_f32(R, "R")
+    _dev_f32(A, "A")
+    if not (R.stride(0) == A.stride(0) == S.stride(0)):
+        raise ValueError("S, R and A must share one leading dimension")
+    dec = torch.empty(n, dtype=torch.int32, device=S.device) if decisions else None
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every),
+                 AP_FLAG_TIME_SWEEP if time_sweep else 0)
+    res = ApResult()
+    ws = workspace(lib().ap_iterate_workspace_size(n, S.stride(0)), S.device)
+    st = lib().ap_iterate(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
+                          C.c_void_p(A.data_ptr()), n, S.stride(0), C.byref(p),
+                          C.c_void_p(dec.data_ptr()) if dec is not None else None,
+                          C.byref(res), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check("ap_iterate", st)
+    return R, A, res.as_dict(), dec
+
+
+def ap_exemplars(S, R, A, stream=None):
+    """Labels idx (int32, -1 without exemplars) and dpsim/expref/netsim."""
+    for t, nm in ((S, "S"), (R, "R"), (A, "A")):
+        _dev_f32(t, nm)
+    n = S.shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device=S.device)
+    res = ApResult()
+    ws = workspace(lib().ap_exemplars_workspace_size(n), S.device)
+    st = lib().ap_exemplars(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
+                            C.c_void_p(A.data_ptr()), n, S.stride(0),
+                            C.c_void_p(idx.data_ptr()), C.byref(res),
+                            C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check("ap_exemplars", st)
+    return idx, res.as_dict()

@@ -1,0 +1,299 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Protocol for the sweep: the test builds S with the oracle in float64 and
+rounds it to float32; the GPU gets those bits and the oracle gets the same
+values widened back to float64, so the only difference is the arithmetic of
+the updates.  R/A error is the infinity-norm relative error
+max|X_gpu - X_ref| / max|X_ref|, bounded by 1e-4.  Decisions that floating
+point takes (the a+r arg-max) are taken in float32 by both sides."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ap as oap
+from paper_0910_1650_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def dev_square(M, ld=None):
+    """float32 device copy of an N x N array with a padded leading dimension."""
+    n = M.shape[0]
+    ld = ld or capi.padded_ld(n)
+    base = torch.full((n, ld), float("nan"), dtype=torch.float32, device="cuda")
+    base[:, :n] = torch.from_numpy(np.ascontiguousarray(M, dtype=np.float32)).cuda()
+    return base[:, :n]
+
+
+def host(T):
+    return T.detach().cpu().numpy().astype(np.float64)
+
+
+def rel_inf(x, ref):
+    return float(np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def s32(X, **kw):
+    S, p = oap.build_similarity(X, **kw)
+    return S.astype(np.float32).astype(np.float64)
+
+
+def workload_S(name):
+    if name == "mix2d_500":
+        X, _ = synth.gaussian_mixture_2d()
+    elif name == "mix64_2000":
+        X, _ = synth.workload(1, scale=0.1)
+    elif name == "small_37":
+        X, _ = synth.gaussian_mixture_2d(n_clusters=3, per_cluster=12)
+        X = X[:37]
+    elif name == "ragged_5003":
+        X, _ = synth.gaussian_mixture(5003, 8, 12, 77, 4.0, 1.0)
+    elif name == "cluster4_9001":
+        X, _ = synth.gaussian_mixture(9001, 16, 20, 78, 5.0, 1.0)
+    else:
+        raise KeyError(name)
+    return s32(X)
+
+
+@pytest.mark.parametrize("name,lam,iters", [
+    ("small_37", 0.5, 1), ("small_37", 0.5, 10), ("small_37", 0.0, 3),
+    # the 500-point mixture at lambda=0.5 passes through a transient (t ~ 20..60)
+    # in which float32 rounding is amplified ~1e5-fold (the float32 oracle differs
+    # from the float64 one by 5e-2 at t=50); parity is taken before and after it
+    ("mix2d_500", 0.5, 1), ("mix2d_500", 0.5, 10), ("mix2d_500", 0.5, 100),
+    ("mix64_2000", 0.9, 1), ("mix64_2000", 0.9, 10), ("mix64_2000", 0.9, 50),
+    ("ragged_5003", 0.9, 5), ("cluster4_9001", 0.9, 3),
+])
+def test_sweep_matches_oracle_fixed_iterations(name, lam, iters):
+    S = workload_S(name)
+    Sd = dev_square(S)
+    R, A, res, dec = capi.ap_iterate(Sd, damping=lam, max_iter=iters, conv_iter=0)
+    torch.cuda.synchronize()
+    ref = oap.run(S, lam=lam, fixed_iters=iters)
+    assert res["iters"] == iters and res["converged"] == 0
+    assert rel_inf(host(R), ref["R"]) <= TOL
+    assert rel_inf(host(A), ref["A"]) <= TOL
+    # decisions after the last iteration, taken in float32 from the GPU's messages
+    got = dec.cpu().numpy()
+    want = oap.decisions(host(R), host(A), dtype=np.float32)
+    assert np.array_equal(got, want)
+
+
+def test_sweep_warm_start_and_padding():
+    """Nonzero initial R/A (the Step 4 use of Algorithm 2) and an ld with
+    padding columns that must stay untouched."""
+    S = workload_S("mix2d_500")
+    n = S.shape[0]
+    g = np.random.default_rng(5)
+    R0 = g.normal(size=(n, n)).astype(np.float32).astype(np.float64)
+    A0 = (-np.abs(g.normal(size=(n, n)))).astype(np.float32).astype(np.float64)
+    ld = capi.padded_ld(n) + 32
+    Sd, Rd, Ad = dev_square(S, ld), dev_square(R0, ld), dev_square(A0, ld)
+    pad_before = [t.as_strided((n, ld - n), (ld, 1), n).clone() for t in (Rd, Ad)]
+    R, A, res, _ = capi.ap_iterate(Sd, Rd, Ad, damping=0.7, max_iter=7, conv_iter=0)
+    torch.cuda.synchronize()
+    ref = oap.run(S, lam=0.7, fixed_iters=7, R0=R0, A0=A0)
+    assert rel_inf(host(R), ref["R"]) <= TOL and rel_inf(host(A), ref["A"]) <= TOL
+    for t, before in zip((Rd, Ad), pad_before):
+        after = t.as_strided((n, ld - n), (ld, 1), n)
+        assert torch.isnan(after).all() and torch.isnan(before).all()
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 31, 65])
+def test_sweep_tiny_sizes(n):
+    g = np.random.default_rng(n)
+    X = g.normal(size=(n, 3))
+    S = s32(X)
+    R, A, res, _ = capi.ap_iterate(dev_square(S), damping=0.5, max_iter=6, conv_iter=0)
+    ref = oap.run(S, lam=0.5, fixed_iters=6)
+    assert rel_inf(host(R), ref["R"]) <= TOL and rel_inf(host(A), ref["A"]) <= TOL
+
+
+@pytest.mark.parametrize("name,lam,maxit", [("mix2d_500", 0.5, 200), ("mix64_2000", 0.9, 1000)])
+def test_convergence_matches_oracle(name, lam, maxit):
+    S = workload_S(name)
+    Sd = dev_square(S)
+    R, A, res, _ = capi.ap_iterate(Sd, damping=lam, max_iter=maxit, conv_iter=15)
+    idx, ex = capi.ap_exemplars(Sd, R, A)
+    ref = oap.run(S, lam=lam, max_iter=maxit, convits=15)
+    eo = oap.exemplars(S, ref["R"], ref["A"])
+    assert res["converged"] == 1 and ref["converged"]
+    # the stopping iteration is not unique across precisions (float32 and float64
+    # cross the transient at slightly different times); the exemplars and labels are
+    assert abs(res["iters"] - ref["iters"]) <= max(5, 0.15 * ref["iters"])
+    assert ex["n_exemplars"] == eo["E"].size
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), eo["idx"])
+    assert abs(ex["netsim"] - eo["netsim"]) <= 1e-9 * abs(eo["netsim"])
+
+
+def test_exemplars_parity_same_bits():
+    """ap_exemplars on given float32 S, R, A: labels exact, sums to float64
+    rounding; the a+r arg-max is taken in float32 by both sides."""
+    S = workload_S("mix2d_500")
+    ref = oap.run(S, lam=0.5, fixed_iters=40)
+    R32 = ref["R"].astype(np.float32).astype(np.float64)
+    A32 = ref["A"].astype(np.float32).astype(np.float64)
+    idx, ex = capi.ap_exemplars(dev_square(S), dev_square(R32), dev_square(A32))
+    eo = oap.exemplars(S, R32, A32, dtype=np.float32)
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), eo["idx"])
+    assert ex["n_exemplars"] == eo["E"].size
+    for k in ("dpsim", "expref", "netsim"):
+        assert abs(ex[k] - eo[k]) <= 1e-12 * abs(eo[k])
+
+
+def test_exemplars_none():
+    S = np.array([[-100.0, -1.0], [-1.0, -100.0]])
+    A = np.array([[-5.0, 0.0], [0.0, -5.0]])
+    idx, ex = capi.ap_exemplars(dev_square(S), dev_square(np.zeros((2, 2))), dev_square(A))
+    assert ex["n_exemplars"] == 0 and (idx.cpu().numpy() == -1).all()
+    assert ex["status"] == capi.AP_NO_EXEMPLARS
+
+
+def test_nonfinite_similarity_rejected():
+    S = workload_S("small_37")
+    S[3, 7] = np.nan
+    with pytest.raises(capi.ApgbError) as e:
+        capi.ap_iterate(dev_square(S), damping=0.5, max_iter=3, conv_iter=0)
+    assert e.value.status == -5
+
+
+def test_invalid_arguments():
+    S = dev_square(workload_S("small_37"))
+    for kw in (dict(damping=1.0), dict(damping=-0.1), dict(max_iter=0)):
+        args = dict(damping=0.5, max_iter=3, conv_iter=0)
+        args.update(kw)
+        with pytest.raises(capi.ApgbError) as e:
+            capi.ap_iterate(S, **args)
+        assert e.value.status == -1
+    one = dev_square(np.zeros((1, 1)))
+    with pytest.raises(capi.ApgbError):
+        capi.ap_iterate(one, damping=0.5, max_iter=3, conv_iter=0)
+
+
+def test_deterministic_bitwise():
+    S = dev_square(workload_S("ragged_5003"))
+    a = capi.ap_iterate(S, damping=0.9, max_iter=4, conv_iter=0)
+    b = capi.ap_iterate(S, damping=0.9, max_iter=4, conv_iter=0)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_resume_reproduces_uninterrupted_run():
+    """Checkpoint/resume: 6 iterations then 5 from the saved (R, A) equal 11
+    straight iterations bitwise."""
+    S = dev_square(workload_S("mix64_2000"))
+    R1, A1, _, _ = capi.ap_iterate(S, damping=0.9, max_iter=6, conv_iter=0)
+    n = S.shape[0]
+    Rc = capi.empty_square(n, S.device)
+    Ac = capi.empty_square(n, S.device)
+    Rc.copy_(R1)
+    Ac.copy_(A1)
+    R2, A2, _, _ = capi.ap_iterate(S, Rc, Ac, damping=0.9, max_iter=5, conv_iter=0)
+    R3, A3, _, _ = capi.ap_iterate(S, damping=0.9, max_iter=11, conv_iter=0)
+    assert torch.equal(R2, R3) and torch.equal(A2, A3)
+
+
+def test_sweep_timing_flag():
+    S = dev_square(workload_S("mix64_2000"))
+    _, _, res, _ = capi.ap_iterate(S, damping=0.9, max_iter=20, conv_iter=0, time_sweep=True)
+    assert res["sweep_launches"] == 21 and res["sweep_ms"] > 0
+
+
+# --- similarity and preference ------------------------------------------------------
+
+def _sim_bound(X):
+    """Per-entry bound for the centred float32 norm form: |err| <=
+    4 (d+4) 2^-24 (|x_i|^2 + |x_k|^2) with x centred."""
+    Xc = X.astype(np.float64) - X.astype(np.float64).mean(axis=0)
+    nrm = (Xc ** 2).sum(axis=1)
+    d = X.shape[1]
+    return 4.0 * (d + 4) * 2.0 ** -24 * (nrm[:, None] + nrm[None, :]) + 1e-30
+
+
+@pytest.mark.parametrize("wl", ["mix2d_500", "mix64_2000", "subspace_1500"])
+def test_similarity_fp32_matches_oracle(wl):
+    if wl == "mix2d_500":
+        X, _ = synth.gaussian_mixture_2d()
+    elif wl == "mix64_2000":
+        X, _ = synth.workload(1, scale=0.1)
+    else:
+        X, _ = synth.workload(2, scale=0.025)
+    Xd = torch.from_numpy(X).cuda()
+    Sd, p = capi.ap_similarity(Xd, precision="fp32")
+    S = host(Sd)
+    So = oap.similarity(X)
+    n = X.shape[0]
+    off = ~np.eye(n, dtype=bool)
+    assert (np.abs(S - So)[off] <= _sim_bound(X)[off]).all()
+    assert (S[off] <= 0).all()
+    # the preference is the exact median of the matrix the kernel produced
+    m = np.median(S[off].astype(np.float32).astype(np.float64))
+    assert p == np.float32(m)
+    assert (np.diag(S) == np.float32(p)).all()
+
+
+def test_preference_median_exact():
+    for n in (2, 3, 100, 1001):
+        g = np.random.default_rng(n)
+        S = (-g.random((n, n)) * 7).astype(np.float32).astype(np.float64)
+        S[g.random((n, n)) < 0.2] = -3.5          # heavy ties
+        got = capi.ap_preference_median(dev_square(S))
+        assert got == np.float32(oap.offdiag_median(S))
+
+
+def test_tiebreak_noise_uses_the_counter_generator():
+    X, _ = synth.gaussian_mixture_2d(per_cluster=30)
+    Sd, p = capi.ap_similarity(torch.from_numpy(X).cuda(), precision="fp32",
+                               pref=-20.0, noise_rel=1e-3, seed=12345)
+    S = host(Sd)
+    So, _ = oap.build_similarity(X, pref=-20.0, noise_rel=1e-3, seed=12345)
+    n = X.shape[0]
+    tol = _sim_bound(X) * 1.01 + 4 * 2.0 ** -24 * np.abs(So)
+    assert (np.abs(S - So) <= tol).all()
+    # without the noise the difference would be of the noise's size
+    S0 = oap.build_similarity(X, pref=-20.0)[0]
+    assert np.abs(S0 - So).max() > 100 * tol.max()
+
+
+def _end_to_end(X, lam, maxit, noise_rel=1e-12, seed=synth.config_seed(0)):
+    Sd, p = capi.ap_similarity(torch.from_numpy(X).cuda(), precision="fp32",
+                               noise_rel=noise_rel, seed=seed)
+    R, A, res, _ = capi.ap_iterate(Sd, damping=lam, max_iter=maxit, conv_iter=15)
+    idx, ex = capi.ap_exemplars(Sd, R, A)
+    So, po = oap.build_similarity(X, noise_rel=noise_rel, seed=seed)
+    ro = oap.run(So, lam=lam, max_iter=maxit, convits=15)
+    eo = oap.exemplars(So, ro["R"], ro["A"])
+    return idx.cpu().numpy().astype(np.int64), ex, p, eo, po, So
+
+
+@pytest.mark.parametrize("case", ["mix2d_500_lam09", "mix64_2000_lam09"])
+def test_end_to_end_identical_exemplars(case):
+    """Features -> S (GPU, float32, median preference, 1e-12 noise) -> AP ->
+    exemplars, against the oracle's float64 S built from the same features:
+    on well-conditioned inputs the exemplars and labels are identical."""
+    if case == "mix2d_500_lam09":
+        X, _ = synth.gaussian_mixture_2d()
+    else:
+        X, _ = synth.workload(1, scale=0.1)
+    lam, maxit = 0.9, 1000
+    idx, ex, p, eo, po, _ = _end_to_end(X, lam, maxit)
+    assert np.array_equal(idx, eo["idx"])
+    assert abs(p - po) <= 1e-5 * abs(po)
+    assert abs(ex["netsim"] - eo["netsim"]) <= 1e-5 * abs(eo["netsim"])
+
+
+def test_end_to_end_ill_conditioned_mixture_lambda05():
+    """The 500-point mixture at lambda=0.5 ends in an exemplar set that depends
+    on ulp-level details of S (a 1e-7 relative change of S already changes it,
+    see the matching CPU test), so the float32 result is checked for validity
+    and quality instead: a self-consistent labelling whose net similarity is
+    within 2% of the float64 oracle's."""
+    X, _ = synth.gaussian_mixture_2d()
+    idx, ex, p, eo, po, So = _end_to_end(X, 0.5, 200)
+    E = np.unique(idx)
+    assert (idx[E] == E).all() and ex["n_exemplars"] == E.size
+    best = np.argmax(So[:, E], axis=1)
+    nonex = np.setdiff1d(np.arange(len(idx)), E)
+    assert (So[nonex, idx[nonex]] >= So[nonex, E[best[nonex]]] - 1e-3).all()
+    assert ex["netsim"] >= eo["netsim"] * 1.02

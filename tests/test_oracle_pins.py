@@ -423,3 +423,50 @@ def test_hand_pins_catch_planted_mistake(golden_dir, name):
         R, A = it(Sr, R, A, 0.5)
     literal_ok = np.abs(R - lit["R"]).max() <= 1e-9 and np.abs(A - lit["A"]).max() <= 1e-9
     assert not (hand_ok and literal_ok)
+
+
+def test_float32_transient_amplification():
+    """Why the float32 parity points of the 500-point mixture at lambda=0.5 avoid
+    t ~ 20..60: there the iteration is ill-conditioned and the same updates in
+    float32 drift from float64 by more than 1e-3, then contract again."""
+    from paper_0910_1650_gb300 import synth
+    X, _ = synth.gaussian_mixture_2d()
+    S32 = ap.build_similarity(X)[0].astype(np.float32)
+    S64 = S32.astype(np.float64)
+    R32 = np.zeros_like(S32)
+    A32 = np.zeros_like(S32)
+    R64 = np.zeros_like(S64)
+    A64 = np.zeros_like(S64)
+    err = {}
+    for t in range(1, 101):
+        R32, A32 = ap.iterate_once(S32, R32, A32, np.float32(0.5))
+        R64, A64 = ap.iterate_once(S64, R64, A64, 0.5)
+        if t in (10, 50, 100):
+            err[t] = np.abs(R32 - R64).max() / np.abs(R64).max()
+    assert err[10] < 1e-5 and err[50] > 1e-3 and err[100] < 1e-5
+
+
+def test_lambda05_mixture_is_ill_conditioned_in_S():
+    """A 1e-7 relative perturbation of S (the centred float32 norm form of the
+    same distances) changes the exemplar set reached at lambda=0.5 but not at
+    lambda=0.9 -- why end-to-end parity at lambda=0.5 checks quality, not
+    identity."""
+    from paper_0910_1650_gb300 import synth
+    X, _ = synth.gaussian_mixture_2d()
+    n = X.shape[0]
+    mean = X.astype(np.float64).mean(axis=0).astype(np.float32)
+    Xc = (X - mean).astype(np.float32)
+    nrm = (Xc * Xc).sum(axis=1, dtype=np.float32)
+    Sg = np.minimum(np.float32(2) * (Xc @ Xc.T) - nrm[:, None] - nrm[None, :],
+                    np.float32(0)).astype(np.float64)
+    Sg = ap.set_preference(Sg, np.float32(ap.offdiag_median(Sg)))
+    S64, _ = ap.build_similarity(X)
+    off = ~np.eye(n, dtype=bool)
+    assert (np.abs(Sg - S64)[off] / np.abs(S64).max()).max() < 1e-6
+    E = {}
+    for nm, S in (("g", Sg), ("d", S64)):
+        for lam, mi in ((0.5, 200), (0.9, 1000)):
+            r = ap.run(S, lam=lam, max_iter=mi)
+            E[nm, lam] = tuple(ap.exemplars(S, r["R"], r["A"])["E"])
+    assert E["g", 0.5] != E["d", 0.5]
+    assert E["g", 0.9] == E["d", 0.9]
