@@ -144,7 +144,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     capi.lib()
 
-    X, _ = synth.workload(1)
+    X, _ = synth.workload(1, scale=args.n / N_POINTS)
     n, d = X.shape
     Xd = torch.from_numpy(X).to(dev)
     Xh = torch.from_numpy(X).pin_memory()
@@ -198,11 +198,15 @@ def run_gpu(args):
     value = float(tot_bytes.item()) / elapsed_max / 1e9
 
     # ---- end to end through the C ABI: host features in, labels out ------------
+    if args.no_e2e:
+        args_steps_e2e = 0
+    else:
+        args_steps_e2e = args.steps
     barrier()
     e0 = time.perf_counter()
     ev0.record(stream)
     e_iters = 0
-    for _ in range(args.steps):
+    for _ in range(args_steps_e2e):
         Xs = Xh.to(dev, non_blocking=True)
         res, ex, idx = step(Xs)
         lab = idx.to("cpu")
@@ -335,6 +339,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=N_POINTS,
+                    help="points (default: the 20000-point workload; smaller for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -45,6 +45,7 @@ extern "C" {
 #define AP_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up       */
 #define AP_ERR_NONFINITE     -5   /* S holds NaN or +-Inf                     */
 #define AP_ERR_UNSUPPORTED   -6   /* e.g. the GPU is not sm_103               */
+#define AP_ERR_TOO_LARGE     -7   /* n exceeds a fixed built-in scratch area  */
 
 /* ---- options --------------------------------------------------------------- */
 #define AP_PREC_FP32   0   /* similarity by a float32 SIMT GEMM                  */
@@ -169,6 +170,34 @@ size_t    ap_exemplars_workspace_size(int64_t n);
 int32_t   ap_exemplars(const float* S, const float* R, const float* A,
                        int64_t n, int64_t ld, int32_t* idx, ap_result* out,
                        void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ap_exemplars_noalloc -- the same computation and outputs as ap_exemplars,
+ * for callers that cannot allocate device memory: plain C callers that only
+ * hold pointers into buffers someone else handed them, callers whose device
+ * memory is entirely reserved by another framework's caching pool, and code
+ * on latency-critical paths where a cudaMalloc would synchronise the device.
+ * The paper has no counterpart; this entry exists for deployment only.
+ *
+ * Instead of a workspace it uses a scratch array built into the library
+ * (a file-scope __device__ array of AP_NOALLOC_SCRATCH_BYTES bytes, which
+ * every GPU that loads the library keeps until the process exits), so it
+ * accepts n <= AP_NOALLOC_MAX_N and returns AP_ERR_TOO_LARGE otherwise.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.  The caller
+ * still passes S, R, A, idx and out.
+ *  - The first call on each device looks up the array's device address
+ *    (with that device current) and caches it; make that first call before
+ *    any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's
+ *    contents; nothing in it needs to start at zero (every scratch word is
+ *    written before it is read).  Calls whose GPU work overlaps (different
+ *    streams, different host threads) race on the array: serialise them.
+ * ------------------------------------------------------------------------- */
+#define AP_NOALLOC_MAX_N         65536
+#define AP_NOALLOC_SCRATCH_BYTES (2u << 20)
+int32_t   ap_exemplars_noalloc(const float* S, const float* R, const float* A,
+                               int64_t n, int64_t ld, int32_t* idx, ap_result* out,
+                               void* stream);
 
 /* ---- misc ------------------------------------------------------------------ */
 const char* ap_status_string(int32_t status);

@@ -23,6 +23,8 @@ AP_NO_EXEMPLARS = 2
 AP_PREC_FP32, AP_PREC_BF16 = 0, 1
 AP_PREF_MEDIAN, AP_PREF_SCALAR, AP_PREF_VECTOR = 0, 1, 2
 AP_FLAG_TIME_SWEEP = 1
+AP_ERR_TOO_LARGE = -7
+AP_NOALLOC_MAX_N = 65536
 
 
 class ApParams(C.Structure):
@@ -62,6 +64,7 @@ _SIGNATURES = {
                                C.POINTER(ApResult), _P, _SZ, _P]),
     "ap_exemplars_workspace_size": (_SZ, [_I64]),
     "ap_exemplars": (C.c_int32, [_P, _P, _P, _I64, _I64, _P, C.POINTER(ApResult), _P, _SZ, _P]),
+    "ap_exemplars_noalloc": (C.c_int32, [_P, _P, _P, _I64, _I64, _P, C.POINTER(ApResult), _P]),
     "ap_status_string": (C.c_char_p, [C.c_int32]),
     "ap_version": (C.c_int32, []),
     "ap_kernel_launches": (C.c_uint64, []),
@@ -221,4 +224,21 @@ def ap_exemplars(S, R, A, stream=None):
                             C.c_void_p(idx.data_ptr()), C.byref(res),
                             C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _check("ap_exemplars", st)
+    return idx, res.as_dict()
+
+
+def ap_exemplars_noalloc(S, R, A, idx=None, stream=None):
+    """ap_exemplars without a workspace: the library's built-in scratch array
+    is used instead (n <= AP_NOALLOC_MAX_N), so no device memory is
+    allocated by the call.  ``idx`` (int32, n) may be passed preallocated."""
+    for t, nm in ((S, "S"), (R, "R"), (A, "A")):
+        _dev_f32(t, nm)
+    n = S.shape[0]
+    if idx is None:
+        idx = torch.empty(n, dtype=torch.int32, device=S.device)
+    res = ApResult()
+    st = lib().ap_exemplars_noalloc(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
+                                    C.c_void_p(A.data_ptr()), n, S.stride(0),
+                                    C.c_void_p(idx.data_ptr()), C.byref(res), _stream(stream))
+    _check("ap_exemplars_noalloc", st)
     return idx, res.as_dict()

@@ -5,6 +5,7 @@
 //   netsim = dpsim + expref                             (float64, fixed order)
 #include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -197,4 +198,54 @@ APGB_API int32_t ap_exemplars(const float* S, const float* R, const float* A, in
     out->iters = iters;
     out->converged = conv;
     return exemplars_impl(S, R, A, n, ld, idx, out, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// No-allocation variant: the workspace is a fixed array inside the library.
+// ---------------------------------------------------------------------------
+namespace apgb {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AP_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];
+
+// Device address of the scratch array for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+static int32_t noalloc_scratch(void** ptr) {
+    int dev = 0;
+    AP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return AP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return AP_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return AP_OK;
+}
+
+}  // namespace apgb
+
+APGB_API int32_t ap_exemplars_noalloc(const float* S, const float* R, const float* A,
+                                      int64_t n, int64_t ld, int32_t* idx, ap_result* out,
+                                      void* stream) {
+    if (!S || !R || !A || !idx || !out) return AP_ERR_INVALID_ARG;
+    if (n < 1 || ld < n || (ld & 3) || !aligned16(R) || !aligned16(A)) return AP_ERR_INVALID_ARG;
+    if (n > AP_NOALLOC_MAX_N || exemplars_ws_bytes(n) > AP_NOALLOC_SCRATCH_BYTES)
+        return AP_ERR_TOO_LARGE;
+    AP_TRY(require_sm103());
+    void* scratch = nullptr;
+    AP_TRY(noalloc_scratch(&scratch));
+    const int32_t iters = out->iters, conv = out->converged;
+    *out = ap_result{};
+    out->iters = iters;
+    out->converged = conv;
+    return exemplars_impl(S, R, A, n, ld, idx, out, scratch, AP_NOALLOC_SCRATCH_BYTES,
+                          static_cast<cudaStream_t>(stream));
 }

@@ -53,6 +53,7 @@ APGB_API const char* ap_status_string(int32_t s) {
         case AP_ERR_TIMEOUT: return "device-side wait timed out";
         case AP_ERR_NONFINITE: return "non-finite similarity";
         case AP_ERR_UNSUPPORTED: return "unsupported device or configuration";
+        case AP_ERR_TOO_LARGE: return "problem larger than the built-in scratch of a no-allocation entry";
         default: return "unknown status";
     }
 }
