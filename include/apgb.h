@@ -157,6 +157,39 @@ int32_t   ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
                      ap_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Launch configuration of the ap_iterate sweep, and its autotuner.
+ *
+ * A cluster of `cluster` CTAs spans one row; each CTA owns a slice of the
+ * columns, `ept` float4 columns per thread, and stages `stages` rows of its
+ * slices of S, R and A in shared memory.  ap_sweep_get_config reports what
+ * ap_iterate would use for n points (a pinned configuration, else the
+ * built-in heuristic); ap_sweep_set_config pins one for n (NULL unpins).
+ * Re-query ap_iterate_workspace_size after pinning: the workspace depends on
+ * the configuration.
+ *
+ * ap_sweep_autotune times every admissible configuration for `iters`
+ * fixed iterations on the caller's S (R and A are overwritten: they are
+ * tuning scratch), pins the fastest for n and returns it.  Its workspace must
+ * hold ap_sweep_autotune_workspace_size(n, ld) bytes.  Synchronous.
+ * ------------------------------------------------------------------------- */
+typedef struct ap_sweep_config {
+    int32_t cluster;    /* 1, 2, 4, 8 or 16                                      */
+    int32_t ept;        /* 1..4                                                  */
+    int32_t stages;     /* 2..4                                                  */
+    int32_t threads;    /* out: threads per CTA                                  */
+    int32_t clusters;   /* out: resident clusters launched                       */
+    int32_t smem_bytes; /* out: dynamic shared memory per CTA                    */
+    float   ms_per_iter;/* out (autotune only): measured time per iteration     */
+    int32_t pad;
+} ap_sweep_config;
+int32_t   ap_sweep_get_config(int64_t n, ap_sweep_config* out);
+int32_t   ap_sweep_set_config(int64_t n, const ap_sweep_config* cfg);
+size_t    ap_sweep_autotune_workspace_size(int64_t n, int64_t ld);
+int32_t   ap_sweep_autotune(const float* S, float* R, float* A, int64_t n, int64_t ld,
+                            float damping, int32_t iters, ap_sweep_config* best,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * ap_exemplars -- outputs of Algorithm 1 from final messages.
  * E = {k : argmax_j (a(k,j)+r(k,j)) == k} (lowest index on ties); exemplars
  * keep idx(k) = k, every other point takes the exemplar of highest s(i,k)

@@ -42,6 +42,15 @@ class ApResult(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class ApSweepConfig(C.Structure):
+    _fields_ = [("cluster", C.c_int32), ("ept", C.c_int32), ("stages", C.c_int32),
+                ("threads", C.c_int32), ("clusters", C.c_int32), ("smem_bytes", C.c_int32),
+                ("ms_per_iter", C.c_float), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class ApgbError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -62,6 +71,11 @@ _SIGNATURES = {
     "ap_iterate_workspace_size": (_SZ, [_I64, _I64]),
     "ap_iterate": (C.c_int32, [_P, _P, _P, _I64, _I64, C.POINTER(ApParams), _P,
                                C.POINTER(ApResult), _P, _SZ, _P]),
+    "ap_sweep_get_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
+    "ap_sweep_set_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
+    "ap_sweep_autotune_workspace_size": (_SZ, [_I64, _I64]),
+    "ap_sweep_autotune": (C.c_int32, [_P, _P, _P, _I64, _I64, C.c_float, C.c_int32,
+                                      C.POINTER(ApSweepConfig), _P, _SZ, _P]),
     "ap_exemplars_workspace_size": (_SZ, [_I64]),
     "ap_exemplars": (C.c_int32, [_P, _P, _P, _I64, _I64, _P, C.POINTER(ApResult), _P, _SZ, _P]),
     "ap_exemplars_noalloc": (C.c_int32, [_P, _P, _P, _I64, _I64, _P, C.POINTER(ApResult), _P]),
@@ -209,6 +223,39 @@ def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check
                           C.byref(res), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _check("ap_iterate", st)
     return R, A, res.as_dict(), dec
+
+
+def ap_sweep_get_config(n):
+    c = ApSweepConfig()
+    _check("ap_sweep_get_config", lib().ap_sweep_get_config(int(n), C.byref(c)), ok=(AP_OK,))
+    return c.as_dict()
+
+
+def ap_sweep_set_config(n, cluster=None, ept=None, stages=None):
+    """Pins (cluster, ept, stages) for n; with no arguments, unpins."""
+    if cluster is None:
+        st = lib().ap_sweep_set_config(int(n), None)
+    else:
+        c = ApSweepConfig(int(cluster), int(ept), int(stages), 0, 0, 0, 0.0, 0)
+        st = lib().ap_sweep_set_config(int(n), C.byref(c))
+    _check("ap_sweep_set_config", st, ok=(AP_OK,))
+
+
+def ap_sweep_autotune(S, R=None, A=None, damping=0.9, iters=5, stream=None):
+    """Times every admissible sweep configuration on S (R, A are scratch),
+    pins the fastest for this n and returns it."""
+    _dev_f32(S, "S")
+    n = S.shape[0]
+    R = empty_square(n, S.device, 0.0) if R is None else R
+    A = empty_square(n, S.device, 0.0) if A is None else A
+    ws = workspace(lib().ap_sweep_autotune_workspace_size(n, S.stride(0)), S.device)
+    best = ApSweepConfig()
+    st = lib().ap_sweep_autotune(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
+                                 C.c_void_p(A.data_ptr()), n, S.stride(0), float(damping),
+                                 int(iters), C.byref(best), C.c_void_p(ws.data_ptr()),
+                                 ws.numel(), _stream(stream))
+    _check("ap_sweep_autotune", st, ok=(AP_OK,))
+    return best.as_dict()
 
 
 def ap_exemplars(S, R, A, stream=None):

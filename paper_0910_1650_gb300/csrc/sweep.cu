@@ -25,10 +25,15 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
+#include <functional>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -46,7 +51,8 @@ struct SweepState {
     int32_t conv_iter;
     int32_t final_buf;   // R buffer (0 = caller's R, 1 = workspace) with R_iters
     int32_t nonfinite;   // count of NaN/Inf entries of S
-    int32_t pad[5];
+    int32_t error;       // a bounded wait gave up
+    int32_t pad[4];
 };
 
 struct SweepArgs {
@@ -58,7 +64,9 @@ struct SweepArgs {
     int          n;
     int          n4;       // float4 columns spanning n
     int          w4;       // float4 columns per CTA
+    int          ns;       // pipeline stages
     float        lam;
+    uint32_t     spin_limit;
     const float* cvec;     // r(k,k) + colp(k) of R_{t-1}
     const float* colp;     // colp(k) of R_{t-1}
     float*       pcol;     // [clusters][n] partial column sums of R_t
@@ -68,10 +76,25 @@ struct SweepArgs {
     SweepState*  st;
 };
 
-struct Slot {
+// A CTA's partial row result, exchanged across the cluster (20 bytes sent).
+struct __align__(16) Slot {
     float m1, m2, dv;
-    int   j1, dj;
+    int   j1;
+    int   dj;
     int   pad[3];
+};
+
+constexpr int kMaxStages = 4;
+constexpr int kMaxCluster = 16;
+
+struct Ctl {
+    uint64_t full[kMaxStages];     // stage filled by TMA
+    uint64_t xbar[2];              // peers' slots arrived (by row parity)
+    Slot xs[2][kMaxCluster];       // peers' slots (by row parity, by sender rank)
+    Slot warp_part[16];
+    Slot fin;
+    int abort;
+    int cnt_changes, cnt_ex;
 };
 
 __device__ __forceinline__ float lane(const float4& v, int e) {
@@ -81,8 +104,17 @@ __device__ __forceinline__ void set_lane(float4& v, int e, float x) {
     if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
 }
 
+// Rows are staged through shared memory: thread 0 keeps ns-1 rows of this
+// CTA's slices of S, R_{t-1} and A in flight as 1-D TMA bulk copies (one
+// mbarrier per stage), the threads update the staged values in place, and
+// thread 0 writes the new A and R slices back with bulk asynchronous stores.
+// The per-row cluster exchange pushes each CTA's partial result into every
+// peer's shared memory with st.async, completing on the peer's mbarrier, so
+// no cluster-wide barrier (and no fence over outstanding global stores) sits
+// on the per-row path.
 template <int EPT>
 __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int csize = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -90,11 +122,11 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     const int G = gridDim.x / csize;
     const int T = blockDim.x;
     const int tid = threadIdx.x;
-
-    __shared__ Slot xs[2];          // this CTA's partial result, by row parity
-    __shared__ Slot warp_part[16];
-    __shared__ Slot fin;
-    __shared__ int  cnt_changes, cnt_ex;
+    const int wid = tid >> 5, lid = tid & 31;
+    const int NS = a.ns;
+    const int w4 = a.w4;
+    float4* stage = reinterpret_cast<float4*>(smem);
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem + (size_t)NS * 3 * w4 * sizeof(float4));
 
     SweepState* st = a.st;
     const int t = st->t;
@@ -105,10 +137,45 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     const float* Rin = ((t - 1) & 1) ? a.R1 : a.R0;
     float* Rout = (t & 1) ? a.R1 : a.R0;
 
-    if (tid == 0) { cnt_changes = 0; cnt_ex = 0; }
+    const int f_begin = crank * w4;
+    const int f_end = min(f_begin + w4, a.n4);
+    const int nslice = max(0, f_end - f_begin);
+    const int f_full_end = min(f_end, a.n >> 2);          // float4s entirely inside n
+    const int nfull = max(0, f_full_end - f_begin);
+    const uint32_t slice_bytes = (uint32_t)nslice * 16u;
+    const uint32_t row_bytes = slice_bytes * (doR ? 3u : 2u);
+    const int nrows = (g < a.n) ? (a.n - g + G - 1) / G : 0;
 
-    const int f_begin = crank * a.w4;
-    const int f_end = min(f_begin + a.w4, a.n4);
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) ptx::mbar_init(&ctl->full[s], 1);
+        ptx::mbar_init(&ctl->xbar[0], 1);
+        ptx::mbar_init(&ctl->xbar[1], 1);
+        ptx::fence_mbar_init();
+        ctl->abort = 0;
+        ctl->cnt_changes = 0;
+        ctl->cnt_ex = 0;
+    }
+    __syncthreads();
+    if (csize > 1) cluster.sync();              // peers' barriers exist before any st.async
+
+    auto sS = [&](int s) { return stage + ((size_t)s * 3 + 0) * w4; };
+    auto sR = [&](int s) { return stage + ((size_t)s * 3 + 1) * w4; };
+    auto sA = [&](int s) { return stage + ((size_t)s * 3 + 2) * w4; };
+    int issued = 0;                             // thread 0: rows whose load was issued
+    auto issue = [&](int r) {                   // thread 0 only
+        const int i = g + r * G;
+        const int s = r % NS;
+        ptx::mbar_arrive_expect_tx(&ctl->full[s], row_bytes);
+        if (nslice > 0) {
+            const int64_t off = (int64_t)i * a.ld + 4 * (int64_t)f_begin;
+            if (doR) ptx::bulk_g2s(sS(s), a.S + off, slice_bytes, &ctl->full[s]);
+            ptx::bulk_g2s(sR(s), Rin + off, slice_bytes, &ctl->full[s]);
+            ptx::bulk_g2s(sA(s), a.A + off, slice_bytes, &ctl->full[s]);
+        }
+        issued = r + 1;
+    };
+    if (tid == 0)
+        for (int r = 0; r < min(NS - 1, nrows); ++r) issue(r);
 
     float4 cv[EPT], acc[EPT];
 #pragma unroll
@@ -124,25 +191,20 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
             }
         }
     }
-    __syncthreads();
 
-    int par = 0;
-    for (int i = g; i < a.n; i += G, par ^= 1) {
-        const float* Srow = a.S + (int64_t)i * a.ld;
-        const float* Rrow = Rin + (int64_t)i * a.ld;
-        float* Arow = a.A + (int64_t)i * a.ld;
-        float4 s4[EPT], r4[EPT], a4[EPT];
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int f = f_begin + tid + q * T;
-            if (f < f_end) {
-                s4[q] = __ldcs(reinterpret_cast<const float4*>(Srow) + f);
-                r4[q] = __ldcs(reinterpret_cast<const float4*>(Rrow) + f);
-                a4[q] = __ldcs(reinterpret_cast<const float4*>(Arow) + f);
-            }
-        }
+    uint32_t xphase = 0;                        // warp 0: phase bit per row parity
+    int r = 0;
+    for (; r < nrows; ++r) {
+        const int i = g + r * G;
+        const int s = r % NS;
+        const int par = r & 1;
+        if (!ptx::mbar_wait(&ctl->full[s], (uint32_t)((r / NS) & 1), a.spin_limit)) ctl->abort = 1;
+
+        const float4* S4 = sS(s);
+        float4* R4 = sR(s);
+        float4* A4 = sA(s);
         const float colp_i = doA ? a.colp[i] : 0.f;
-
+        float4 s4[EPT], r4[EPT];
         Top2 tp{-INFINITY, -INFINITY, INT_MAX};
         float dv = -INFINITY;
         int dj = INT_MAX;
@@ -150,88 +212,109 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
         for (int q = 0; q < EPT; ++q) {
             const int f = f_begin + tid + q * T;
             if (f < f_end) {
+                const int x = f - f_begin;
+                s4[q] = doR ? S4[x] : make_float4(0.f, 0.f, 0.f, 0.f);
+                r4[q] = R4[x];
+                float4 a4 = A4[x];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int k = 4 * f + e;
                     if (k < a.n) {
-                        const float s = lane(s4[q], e), r = lane(r4[q], e);
-                        float av = lane(a4[q], e);
+                        const float sv = lane(s4[q], e), rv = lane(r4[q], e);
+                        float av = lane(a4, e);
                         if (doA) {
                             const float an = (k == i) ? colp_i
-                                                      : fminf(0.f, lane(cv[q], e) - fmaxf(0.f, r));
+                                                      : fminf(0.f, lane(cv[q], e) - fmaxf(0.f, rv));
                             av = fmaf(lam, av, oml * an);
-                            set_lane(a4[q], e, av);
-                            argmax_merge(dv, dj, av + r, k);
+                            set_lane(a4, e, av);
+                            argmax_merge(dv, dj, av + rv, k);
                         }
-                        top2_push(tp, av + s, k);
+                        if (doR) top2_push(tp, av + sv, k);
                     }
                 }
                 if (doA) {
-                    float4* dst = reinterpret_cast<float4*>(Arow) + f;
-                    if (4 * f + 3 < a.n) {
-                        __stcs(dst, a4[q]);
+                    if (f < f_full_end) {
+                        A4[x] = a4;
                     } else {
+                        float* Arow = a.A + (int64_t)i * a.ld;
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            if (4 * f + e < a.n) Arow[4 * f + e] = lane(a4[q], e);
+                            if (4 * f + e < a.n) Arow[4 * f + e] = lane(a4, e);
                     }
                 }
             }
         }
 
-        // ---- CTA reduction of (top-2, decision arg-max) -----------------
+        // ---- CTA reduction of (top-2, decision arg-max) -------------------
         tp = top2_warp(tp);
         argmax_warp(dv, dj);
-        const int wid = tid >> 5, lid = tid & 31;
-        if (lid == 0) warp_part[wid] = Slot{tp.m1, tp.m2, dv, tp.j1, dj, {0, 0, 0}};
+        if (lid == 0) ctl->warp_part[wid] = Slot{tp.m1, tp.m2, dv, tp.j1, dj, {0, 0, 0}};
         __syncthreads();
+        if (ctl->abort) break;
         if (wid == 0) {
             const int nw = T >> 5;
             Top2 u{-INFINITY, -INFINITY, INT_MAX};
             float uv = -INFINITY;
             int uj = INT_MAX;
             if (lid < nw) {
-                const Slot p = warp_part[lid];
+                const Slot p = ctl->warp_part[lid];
                 u = Top2{p.m1, p.m2, p.j1};
                 uv = p.dv;
                 uj = p.dj;
             }
             u = top2_warp(u);
             argmax_warp(uv, uj);
-            if (lid == 0) xs[par] = Slot{u.m1, u.m2, uv, u.j1, uj, {0, 0, 0}};
-        }
-        // ---- cluster reduction through distributed shared memory --------
-        if (csize > 1) cluster.sync(); else __syncthreads();
-        if (wid == 0) {
-            Top2 u{-INFINITY, -INFINITY, INT_MAX};
-            float uv = -INFINITY;
-            int uj = INT_MAX;
-            if (lid < csize) {
-                const Slot* rs = csize > 1 ? cluster.map_shared_rank(&xs[par], lid) : &xs[par];
-                const Slot p = *rs;
-                u = Top2{p.m1, p.m2, p.j1};
-                uv = p.dv;
-                uj = p.dj;
+            if (csize > 1) {
+                // ---- cluster exchange: push this CTA's slot into every peer.
+                // Slots are double-buffered by row parity: a peer can write the
+                // row r+2 slot only after it has received this CTA's row r+1
+                // slot, which is sent after the row r slots below were read.
+                Slot* slots = ctl->xs[par];
+                if (lid < csize) {
+                    if (lid == crank) {
+                        slots[crank] = Slot{u.m1, u.m2, uv, u.j1, uj, {0, 0, 0}};
+                    } else {
+                        const uint32_t ra = ptx::mapa(&slots[crank], (uint32_t)lid);
+                        const uint32_t rb = ptx::mapa(&ctl->xbar[par], (uint32_t)lid);
+                        ptx::st_async_v4(ra, __float_as_uint(u.m1), __float_as_uint(u.m2),
+                                         __float_as_uint(uv), (uint32_t)u.j1, rb);
+                        ptx::st_async_b32(ra + 16u, (uint32_t)uj, rb);
+                    }
+                }
+                if (lid == 0) ptx::mbar_arrive_expect_tx(&ctl->xbar[par], 20u * (csize - 1));
+                const bool ok = ptx::mbar_wait(&ctl->xbar[par], (xphase >> par) & 1u, a.spin_limit);
+                xphase ^= 1u << par;
+                __syncwarp();
+                if (!ok && lid == 0) ctl->abort = 1;
+                u = Top2{-INFINITY, -INFINITY, INT_MAX};
+                uv = -INFINITY;
+                uj = INT_MAX;
+                if (lid < csize) {
+                    const Slot p = slots[lid];
+                    u = Top2{p.m1, p.m2, p.j1};
+                    uv = p.dv;
+                    uj = p.dj;
+                }
+                u = top2_warp(u);
+                argmax_warp(uv, uj);
             }
-            u = top2_warp(u);
-            argmax_warp(uv, uj);
-            if (lid == 0) fin = Slot{u.m1, u.m2, uv, u.j1, uj, {0, 0, 0}};
+            if (lid == 0) ctl->fin = Slot{u.m1, u.m2, uv, u.j1, uj, {0, 0, 0}};
         }
         __syncthreads();
-        const float m1 = fin.m1, m2 = fin.m2;
-        const int j1 = fin.j1;
+        if (ctl->abort) break;
+        const float m1 = ctl->fin.m1, m2 = ctl->fin.m2;
+        const int j1 = ctl->fin.j1;
 
         if (doA && crank == 0 && tid == 0) {
-            const int d = fin.dj;
+            const int d = ctl->fin.dj;
             if (a.dec) a.dec[i] = d;
             const int e = (d == i) ? 1 : 0;
-            if (a.eflag[i] != e) ++cnt_changes;
+            if (a.eflag[i] != e) ++ctl->cnt_changes;
             a.eflag[i] = e;
-            cnt_ex += e;
+            ctl->cnt_ex += e;
         }
 
         if (doR) {
-            float* Orow = Rout + (int64_t)i * a.ld;
 #pragma unroll
             for (int q = 0; q < EPT; ++q) {
                 const int f = f_begin + tid + q * T;
@@ -240,19 +323,19 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int k = 4 * f + e;
-                        const float s = lane(s4[q], e), r = lane(r4[q], e);
+                        const float sv = lane(s4[q], e), rv = lane(r4[q], e);
                         const float m = (k == j1) ? m2 : m1;
-                        const float rn = fmaf(lam, r, oml * (s - m));
+                        const float rn = fmaf(lam, rv, oml * (sv - m));
                         set_lane(o, e, rn);
                         if (k < a.n) {
                             if (k == i) a.rkk[i] = rn;
                             else set_lane(acc[q], e, lane(acc[q], e) + fmaxf(0.f, rn));
                         }
                     }
-                    float4* dst = reinterpret_cast<float4*>(Orow) + f;
-                    if (4 * f + 3 < a.n) {
-                        __stcs(dst, o);
+                    if (f < f_full_end) {
+                        R4[f - f_begin] = o;
                     } else {
+                        float* Orow = Rout + (int64_t)i * a.ld;
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             if (4 * f + e < a.n) Orow[4 * f + e] = lane(o, e);
@@ -260,9 +343,33 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
                 }
             }
         }
+        ptx::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            if (nfull > 0) {
+                const int64_t off = (int64_t)i * a.ld + 4 * (int64_t)f_begin;
+                if (doA) ptx::bulk_s2g(a.A + off, A4, (uint32_t)nfull * 16u);
+                if (doR) ptx::bulk_s2g(Rout + off, R4, (uint32_t)nfull * 16u);
+            }
+            ptx::bulk_commit();
+            const int nxt = r + NS - 1;
+            if (nxt < nrows) {
+                ptx::bulk_wait_read<1>();       // stores of row r-1 no longer read its stage
+                issue(nxt);
+            }
+        }
     }
 
-    if (doR) {
+    if (tid == 0) {
+        if (ctl->abort) {
+            // drain the loads already in flight before shared memory goes away
+            for (int q = r; q < issued; ++q)
+                ptx::mbar_wait(&ctl->full[q % NS], (uint32_t)((q / NS) & 1), a.spin_limit);
+            atomicExch(&st->error, 1);
+        }
+        ptx::bulk_wait_all();
+    }
+    if (doR && !ctl->abort) {
         float* P = a.pcol + (int64_t)g * a.n;
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
@@ -276,10 +383,10 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     }
     __syncthreads();
     if (tid == 0 && crank == 0 && doA) {
-        atomicAdd(&st->changes, cnt_changes);
-        atomicAdd(&st->n_ex, cnt_ex);
+        atomicAdd(&st->changes, ctl->cnt_changes);
+        atomicAdd(&st->n_ex, ctl->cnt_ex);
     }
-    // keep this CTA's shared memory alive until every peer has read it
+    // keep this CTA's shared memory alive until every peer is done with it
     if (csize > 1) cluster.sync();
 }
 
@@ -345,7 +452,8 @@ __global__ void nonfinite_kernel(const float* __restrict__ S, int n, int64_t ld,
 // Launch configuration
 // ---------------------------------------------------------------------------
 struct SweepConfig {
-    int C, T, EPT, W4, G;
+    int C, T, EPT, W4, G, NS;
+    size_t smem;
 };
 
 template <int EPT>
@@ -360,12 +468,18 @@ static void* sweep_ptr(int ept) {
     }
 }
 
-static int32_t max_clusters(int ept, int C, int T, int* out) {
+static size_t sweep_smem(int w4, int ns) {
+    return (size_t)ns * 3 * w4 * sizeof(float4) + sizeof(Ctl);
+}
+
+static int32_t max_clusters(int ept, int C, int T, size_t smem, int* out) {
     void* fn = sweep_ptr(ept);
+    AP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (C > 8) AP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(T, 1, 1);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
     attr.val.clusterDim.x = C;
@@ -382,31 +496,52 @@ static int32_t max_clusters(int ept, int C, int T, int* out) {
     return AP_OK;
 }
 
-// Smallest cluster whose slices need at most 2 float4 per thread (<= 512
-// threads), else 4; the thread count is trimmed to balance the slice.
-static int32_t choose_config(int n, SweepConfig* c) {
+// Validates (C, ept, ns) for n and fills the derived launch parameters.
+static int32_t make_config(int n, int C, int ept, int ns, SweepConfig* c) {
+    if (C < 1 || C > kMaxCluster || (C & (C - 1)) || ept < 1 || ept > 4 || ns < 2 ||
+        ns > kMaxStages)
+        return AP_ERR_INVALID_ARG;
     const int n4 = (n + 3) / 4;
-    const int clusters[] = {1, 2, 4, 8, 16};
-    for (int ept_cap : {2, 4}) {
-        for (int C : clusters) {
-            if (C > 1 && n4 < 64 * C) break;
-            const int w4 = (n4 + C - 1) / C;
-            int ept = (w4 + 511) / 512;
-            if (ept < 1) ept = 1;
-            if (ept > ept_cap) continue;
-            if (ept == 3 && ept_cap == 4) ept = 4;
-            int T = ((w4 + ept - 1) / ept + 31) / 32 * 32;
-            T = std::max(T, 64);
-            int num = 0;
-            AP_TRY(max_clusters(ept, C, T, &num));
-            if (num <= 0) continue;
-            c->C = C;
-            c->T = T;
-            c->EPT = ept;
-            c->W4 = w4;
-            c->G = std::max(1, std::min(num, n));
-            return AP_OK;
-        }
+    if (C > 1 && n4 < 8 * C) return AP_ERR_UNSUPPORTED;
+    const int w4 = (n4 + C - 1) / C;
+    int T = ((w4 + ept - 1) / ept + 31) / 32 * 32;
+    T = std::max(T, 64);
+    if (T > 512) return AP_ERR_UNSUPPORTED;
+    const size_t smem = sweep_smem(w4, ns);
+    if (smem > 227 * 1024) return AP_ERR_UNSUPPORTED;
+    int num = 0;
+    AP_TRY(max_clusters(ept, C, T, smem, &num));
+    if (num <= 0) return AP_ERR_UNSUPPORTED;
+    c->C = C;
+    c->T = T;
+    c->EPT = ept;
+    c->W4 = w4;
+    c->NS = ns;
+    c->smem = smem;
+    c->G = std::max(1, std::min(num, n));
+    return AP_OK;
+}
+
+static std::mutex g_pin_mu;
+static std::map<int64_t, std::array<int, 3>> g_pinned;   // n -> (C, ept, ns)
+
+// A stage (S, R and A slices of one row) of about 24-32 KB: the smallest
+// power-of-two cluster whose slice is at most 640 float4 columns, at most 4
+// float4 per thread, and three stages when they fit.  A configuration pinned
+// for n (by ap_sweep_set_config or the autotuner) takes precedence.
+static int32_t choose_config(int n, SweepConfig* c) {
+    {
+        std::lock_guard<std::mutex> lock(g_pin_mu);
+        auto it = g_pinned.find(n);
+        if (it != g_pinned.end()) return make_config(n, it->second[0], it->second[1], it->second[2], c);
+    }
+    const int n4 = (n + 3) / 4;
+    for (int C = 1; C <= kMaxCluster; C *= 2) {
+        const int w4 = (n4 + C - 1) / C;
+        if (w4 > 640 && C < kMaxCluster) continue;
+        int ept = std::min(4, (w4 + 383) / 384);
+        for (int ns : {3, 2})
+            if (make_config(n, C, ept, ns, c) == AP_OK) return AP_OK;
     }
     return AP_ERR_UNSUPPORTED;
 }
@@ -440,6 +575,8 @@ struct SweepWs {
 };
 
 static size_t carve_sweep(void* ws, int64_t n, int64_t ld, int G, SweepWs* w) {
+    SweepWs dummy;
+    if (!w) w = &dummy;
     Carver cv(ws);
     w->R1 = cv.take<float>((size_t)n * ld);
     w->pcol = cv.take<float>((size_t)G * n);
@@ -452,9 +589,12 @@ static size_t carve_sweep(void* ws, int64_t n, int64_t ld, int G, SweepWs* w) {
 }
 
 static int32_t launch_sweep(const SweepConfig& c, const SweepArgs& args, cudaStream_t s) {
+    AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)c.smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.C * c.G, 1, 1);
     cfg.blockDim = dim3(c.T, 1, 1);
+    cfg.dynamicSmemBytes = c.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
@@ -483,30 +623,11 @@ int32_t sweep_workspace(int64_t n, int64_t ld, size_t* bytes, SweepConfig* cfg_o
     return AP_OK;
 }
 
-}  // namespace apgb
-
-using namespace apgb;
-
-APGB_API size_t ap_iterate_workspace_size(int64_t n, int64_t ld) {
-    size_t b = 0;
-    if (sweep_workspace(n, ld, &b, nullptr) != AP_OK) return 0;
-    return b;
-}
-
-APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
-                            const ap_params* p, int32_t* decisions, ap_result* out,
-                            void* ws, size_t ws_bytes, void* stream) {
-    if (!S || !R || !A || !p) return AP_ERR_INVALID_ARG;
-    if (n < 2 || ld < n || (ld & 3) || !aligned16(S) || !aligned16(R) || !aligned16(A))
-        return AP_ERR_INVALID_ARG;
-    if (!(p->damping >= 0.f && p->damping < 1.f) || p->max_iter < 1 || p->conv_iter < 0)
-        return AP_ERR_INVALID_ARG;
-    AP_TRY(require_sm103());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    SweepConfig c;
-    size_t need = 0;
-    AP_TRY(sweep_workspace(n, ld, &need, &c));
-    AP_TRY(check_ws(ws, ws_bytes, need));
+// The iteration loop of ap_iterate for a given launch configuration.
+static int32_t run_sweep(const float* S, float* R, float* A, int64_t n, int64_t ld,
+                         const ap_params* p, int32_t* decisions, ap_result* out, void* ws,
+                         size_t ws_bytes, cudaStream_t s, const SweepConfig& c) {
+    AP_TRY(check_ws(ws, ws_bytes, carve_sweep(nullptr, n, ld, c.G, nullptr)));
     SweepWs w;
     carve_sweep(ws, n, ld, c.G, &w);
     const int ni = (int)n;
@@ -529,6 +650,8 @@ APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64
     args.n = ni;
     args.n4 = (ni + 3) / 4;
     args.w4 = c.W4;
+    args.ns = c.NS;
+    args.spin_limit = 1u << 20;
     args.lam = p->damping;
     args.cvec = w.cvec;
     args.colp = w.colp;
@@ -576,6 +699,7 @@ APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64
                 sweep_ms += ms;
             }
         }
+        if (hs.error) return AP_ERR_TIMEOUT;
         if (hs.done) break;
     }
     if (!hs.done) return AP_ERR_CUDA;   // cannot happen: launch max_iter+1 always stops
@@ -593,4 +717,123 @@ APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64
         out->sweep_launches = worked;
     }
     return status;
+}
+
+static void fill_public(const SweepConfig& c, ap_sweep_config* o) {
+    o->cluster = c.C;
+    o->ept = c.EPT;
+    o->stages = c.NS;
+    o->threads = c.T;
+    o->clusters = c.G;
+    o->smem_bytes = (int32_t)c.smem;
+}
+
+static bool valid_iterate_args(const float* S, float* R, float* A, int64_t n, int64_t ld) {
+    return S && R && A && n >= 2 && n <= INT_MAX / 4 && ld >= n && !(ld & 3) && aligned16(S) &&
+           aligned16(R) && aligned16(A);
+}
+
+}  // namespace apgb
+
+using namespace apgb;
+
+APGB_API size_t ap_iterate_workspace_size(int64_t n, int64_t ld) {
+    size_t b = 0;
+    if (sweep_workspace(n, ld, &b, nullptr) != AP_OK) return 0;
+    return b;
+}
+
+APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
+                            const ap_params* p, int32_t* decisions, ap_result* out,
+                            void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !valid_iterate_args(S, R, A, n, ld)) return AP_ERR_INVALID_ARG;
+    if (!(p->damping >= 0.f && p->damping < 1.f) || p->max_iter < 1 || p->conv_iter < 0)
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    SweepConfig c;
+    size_t need = 0;
+    AP_TRY(sweep_workspace(n, ld, &need, &c));
+    return run_sweep(S, R, A, n, ld, p, decisions, out, ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream), c);
+}
+
+APGB_API int32_t ap_sweep_get_config(int64_t n, ap_sweep_config* out) {
+    if (!out || n < 2 || n > INT_MAX / 4) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    SweepConfig c;
+    AP_TRY(choose_config((int)n, &c));
+    *out = ap_sweep_config{};
+    fill_public(c, out);
+    return AP_OK;
+}
+
+APGB_API int32_t ap_sweep_set_config(int64_t n, const ap_sweep_config* cfg) {
+    if (n < 2 || n > INT_MAX / 4) return AP_ERR_INVALID_ARG;
+    if (!cfg) {
+        std::lock_guard<std::mutex> lock(g_pin_mu);
+        g_pinned.erase(n);
+        return AP_OK;
+    }
+    AP_TRY(require_sm103());
+    SweepConfig c;
+    AP_TRY(make_config((int)n, cfg->cluster, cfg->ept, cfg->stages, &c));
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_pinned[n] = {cfg->cluster, cfg->ept, cfg->stages};
+    return AP_OK;
+}
+
+static void for_each_candidate(int n, const std::function<void(const SweepConfig&)>& f) {
+    for (int C = 1; C <= kMaxCluster; C *= 2)
+        for (int ept = 1; ept <= 4; ++ept)
+            for (int ns = 2; ns <= kMaxStages; ++ns) {
+                SweepConfig c;
+                if (make_config(n, C, ept, ns, &c) == AP_OK) f(c);
+            }
+}
+
+APGB_API size_t ap_sweep_autotune_workspace_size(int64_t n, int64_t ld) {
+    if (n < 2 || n > INT_MAX / 4 || ld < n) return 0;
+    if (require_sm103() != AP_OK) return 0;
+    size_t best = 0;
+    for_each_candidate((int)n, [&](const SweepConfig& c) {
+        best = std::max(best, carve_sweep(nullptr, n, ld, c.G, nullptr));
+    });
+    return best;
+}
+
+APGB_API int32_t ap_sweep_autotune(const float* S, float* R, float* A, int64_t n, int64_t ld,
+                                   float damping, int32_t iters, ap_sweep_config* best,
+                                   void* ws, size_t ws_bytes, void* stream) {
+    if (!best || !valid_iterate_args(S, R, A, n, ld) || iters < 1 ||
+        !(damping >= 0.f && damping < 1.f))
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<SweepConfig> cands;
+    for_each_candidate((int)n, [&](const SweepConfig& c) { cands.push_back(c); });
+    if (cands.empty()) return AP_ERR_UNSUPPORTED;
+    ap_params p{damping, iters, 0, iters + 1, AP_FLAG_TIME_SWEEP};
+    double best_ms = 1e300;
+    SweepConfig best_c = cands[0];
+    for (const SweepConfig& c : cands) {
+        AP_CUDA_TRY(cudaMemset2DAsync(R, ld * sizeof(float), 0, n * sizeof(float), n, s));
+        AP_CUDA_TRY(cudaMemset2DAsync(A, ld * sizeof(float), 0, n * sizeof(float), n, s));
+        ap_result r;
+        const int32_t st = run_sweep(S, R, A, n, ld, &p, nullptr, &r, ws, ws_bytes, s, c);
+        if (st < 0) return st;
+        // the first and last launches do half the work: time the middle ones
+        const double per = r.sweep_ms / std::max(1, r.sweep_launches);
+        if (per < best_ms) {
+            best_ms = per;
+            best_c = c;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_pin_mu);
+        g_pinned[n] = {best_c.C, best_c.EPT, best_c.NS};
+    }
+    *best = ap_sweep_config{};
+    fill_public(best_c, best);
+    best->ms_per_iter = (float)best_ms;
+    return AP_OK;
 }
