@@ -108,7 +108,8 @@ typedef struct ap_result {
  *           53 bits of splitmix64 output number i*n+k+1 of ``seed``, times
  *           2^-53.  noise_rel = 0 skips the pass.
  *  pref_out host float* (may be NULL): receives the scalar preference used
- *           (NaN for AP_PREF_VECTOR).  Non-NULL makes the call synchronous.
+ *           (NaN for AP_PREF_VECTOR).  The call synchronises ``stream``.
+ *  Errors: AP_ERR_TIMEOUT if a bounded wait of the tensor-core kernel gave up.
  * ------------------------------------------------------------------------- */
 size_t    ap_similarity_workspace_size(int64_t n, int64_t d);
 int32_t   ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx,

@@ -55,6 +55,29 @@ def similarity(X: np.ndarray, Y: np.ndarray | None = None) -> np.ndarray:
     return S
 
 
+def round_bf16(x) -> np.ndarray:
+    """float32 -> nearest bfloat16 (ties to even), returned as float32: keep
+    the top 16 bits after adding 0x7FFF plus the lowest kept bit."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def centred(X, dtype=np.float32):
+    """X minus its column mean (mean in float64, rounded to float32; the
+    subtraction in float32), the translation the similarity paths apply
+    before their GEMM; distances are unchanged by it."""
+    X = np.asarray(X, dtype=np.float32)
+    mean = X.astype(np.float64).mean(axis=0).astype(np.float32)
+    return (X - mean).astype(dtype)
+
+
+def similarity_bf16_inputs(X) -> np.ndarray:
+    """The points whose exact negative squared distances the bf16 path
+    computes: the centred features rounded to bfloat16 (as float64)."""
+    return round_bf16(centred(X)).astype(np.float64)
+
+
 def offdiag_median(S: np.ndarray) -> float:
     """Median of the N(N-1) off-diagonal entries: the middle order statistic,
     or the mean of the two middle ones when the count is even."""

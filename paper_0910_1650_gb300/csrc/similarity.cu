@@ -23,7 +23,7 @@
 namespace apgb {
 
 int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int dpad,
-                           float* S, int64_t lds, cudaStream_t s);
+                           float* S, int64_t lds, int32_t* err, cudaStream_t s);
 size_t tc_similarity_pad_rows();
 
 // ---- 1. column means -----------------------------------------------------------
@@ -251,6 +251,7 @@ struct SimWs {
     SelectState* sel;
     unsigned long long* hist;
     float* pref;
+    int32_t* err;
 };
 
 static int pad_rows(int n) {
@@ -270,6 +271,7 @@ static size_t carve_sim(void* ws, int64_t n, int64_t d, SimWs* w) {
     w->sel = c.take<SelectState>(1);
     w->hist = c.take<unsigned long long>(4096);
     w->pref = c.take<float>(1);
+    w->err = c.take<int32_t>(1);
     return c.used;
 }
 
@@ -331,7 +333,9 @@ APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx
     } else {
         centre_kernel<true><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
         AP_TRY(last_error());
-        AP_TRY(tc_similarity_bf16(static_cast<const __nv_bfloat16*>(w.xc), w.nrm, ni, dpad, S, lds, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+        AP_TRY(tc_similarity_bf16(static_cast<const __nv_bfloat16*>(w.xc), w.nrm, ni, dpad, S, lds,
+                                  w.err, s));
     }
 
     float used = NAN;
@@ -350,13 +354,15 @@ APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx
     }
     note_launches(precision == AP_PREC_FP32 ? 5 : 3);   // means(2), centre, GEMM, diagonal
     AP_TRY(last_error());
-    if (pref_out) {
-        float v = used;
-        if (pref_mode == AP_PREF_MEDIAN)
-            AP_CUDA_TRY(cudaMemcpyAsync(&v, w.pref, sizeof(float), cudaMemcpyDeviceToHost, s));
-        AP_CUDA_TRY(cudaStreamSynchronize(s));
-        *pref_out = v;
-    }
+    float v = used;
+    int32_t err = 0;
+    if (pref_mode == AP_PREF_MEDIAN)
+        AP_CUDA_TRY(cudaMemcpyAsync(&v, w.pref, sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (precision == AP_PREC_BF16)
+        AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return AP_ERR_TIMEOUT;
+    if (pref_out) *pref_out = v;
     return AP_OK;
 }
 

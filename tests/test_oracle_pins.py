@@ -470,3 +470,26 @@ def test_lambda05_mixture_is_ill_conditioned_in_S():
             E[nm, lam] = tuple(ap.exemplars(S, r["R"], r["A"])["E"])
     assert E["g", 0.5] != E["d", 0.5]
     assert E["g", 0.9] == E["d", 0.9]
+
+
+# --- bf16 rounding used to state the tensor-core similarity's inputs ----------------
+
+def test_round_bf16_hand_values():
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -2.5, 0.0, 65504.0],
+                    dtype=np.float32)
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties go to the even mantissa (1.0);
+    # 1 + 3*2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6: even is 1 + 2^-6
+    want = np.array([1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -2.5, 0.0, 65536.0], dtype=np.float32)
+    assert np.array_equal(ap.round_bf16(vals), want)
+
+
+def test_round_bf16_vs_torch():
+    torch = pytest.importorskip("torch")
+    x = (np.random.default_rng(3).normal(size=20000) * 100).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(ap.round_bf16(x), want)
+
+
+def test_centring_preserves_distances():
+    X = np.random.default_rng(4).normal(size=(40, 5)).astype(np.float32) + 100
+    assert np.allclose(ap.similarity(ap.centred(X)), ap.similarity(X), rtol=1e-5, atol=1e-3)
