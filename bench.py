@@ -153,13 +153,27 @@ def run_gpu(args):
     A = capi.empty_square(n, dev)
     stream = torch.cuda.current_stream()
 
-    def step(X_in):
+    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    phase_ms = {"similarity": 0.0, "iterate": 0.0, "exemplars": 0.0}
+
+    def step(X_in, timed=False):
+        if timed:
+            phase_ev[0].record(stream)
         capi.ap_similarity(X_in, S, precision=args.precision)
+        if timed:
+            phase_ev[1].record(stream)
         R.zero_()
         A.zero_()
         _, _, res, _ = capi.ap_iterate(S, R, A, damping=DAMPING, max_iter=MAX_ITER,
                                        conv_iter=CONV_ITER, time_sweep=True, decisions=False)
+        if timed:
+            phase_ev[2].record(stream)
         idx, ex = capi.ap_exemplars(S, R, A)
+        if timed:
+            phase_ev[3].record(stream)
+            phase_ev[3].synchronize()
+            for k, (a, b) in zip(("similarity", "iterate", "exemplars"), ((0, 1), (1, 2), (2, 3))):
+                phase_ms[k] += phase_ev[a].elapsed_time(phase_ev[b])
         return res, ex, idx
 
     for _ in range(args.warmup):
@@ -179,7 +193,7 @@ def run_gpu(args):
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
-            res, ex, _ = step(Xd)
+            res, ex, _ = step(Xd, timed=True)
             iters += res["iters"]
             sweep_ms += res["sweep_ms"]
             sweep_launches += res["sweep_launches"]
@@ -249,6 +263,7 @@ def run_gpu(args):
                        "iters_per_step": last_res["iters"],
                        "n_exemplars": last_ex["n_exemplars"], "netsim": last_ex["netsim"],
                        "l2": "inputs larger than L2 (S, R, A 1.6 GB each); no flush",
+                       "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in phase_ms.items()},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"kernel": "sweep_kernel", "bound": "hbm",
                          "achieved": round(achieved, 1) if achieved else None,
@@ -336,7 +351,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
