@@ -158,6 +158,53 @@ int32_t   ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
                      ap_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * ap_iterate_batched -- Algorithm 1 on `count` independent problems in one
+ * launch per iteration (Algorithm 2 Step 2 runs the k sub-matrices this way).
+ * Problem b is the n[b] x n[b] matrix at element offset offsets[b] of the
+ * S, R and A arenas, leading dimension ld[b] (offsets[b] % 4 == 0, ld[b] %
+ * 4 == 0, n[b] >= 2).  Every problem uses `params`; each stops on its own
+ * rule.  The grid's clusters are divided between problems in proportion to
+ * n[b]^2.  offsets, n, ld: host arrays.  decisions: device int32 arena of
+ * sum(n) entries (problem b's after those of problems < b) or NULL.
+ * out: host array of `count` results.  Synchronous.  Returns the largest
+ * per-problem status (AP_NOT_CONVERGED if any problem hit max_iter).
+ * ------------------------------------------------------------------------- */
+size_t    ap_iterate_batched_workspace_size(const int64_t* n, const int64_t* ld, int32_t count);
+int32_t   ap_iterate_batched(const float* S, float* R, float* A, const int64_t* offsets,
+                             const int64_t* n, const int64_t* ld, int32_t count,
+                             const ap_params* params, int32_t* decisions, ap_result* out,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * pap_run -- partition affinity propagation, Algorithm 2 (Section 3).
+ *  Step 1: k diagonal blocks of the given point order: part_offsets (host,
+ *          k+1 entries, 0 = first < ... < last = n) or, when NULL, the
+ *          paper's rule m = floor(n/k) for blocks 1..k-1 and n - m(k-1) for
+ *          block k.
+ *  Step 2: Algorithm 1 on every S_jj (the block of S as it stands, global
+ *          preferences on its diagonal), all blocks in one batched run.
+ *  Step 3: A' = blockdiag(A_11, ..., A_kk), zeros elsewhere, written to A.
+ *  Step 4: Algorithm 1 on the whole S from R = 0 (the paper carries only the
+ *          availabilities) and A = A'.
+ *  Then the outputs of Algorithm 1 (as ap_exemplars) into idx and out->final.
+ *  S device [n x ld]; R, A device [n x ld] outputs (final messages);
+ *  idx device int32 [n].  `params` applies to Steps 2 and 4.  Synchronous.
+ * ------------------------------------------------------------------------- */
+typedef struct pap_result {
+    int32_t   k;
+    int32_t   sub_iters_max;      /* largest Step-2 iteration count          */
+    int64_t   sub_iters_sum;
+    int32_t   sub_not_converged;  /* Step-2 runs that reached max_iter       */
+    int32_t   pad;
+    double    sub_ms, merge_ms, final_ms, exemplars_ms;   /* device time     */
+    ap_result final;              /* Step 4 iterations and the outputs       */
+} pap_result;
+size_t    pap_run_workspace_size(int64_t n, int64_t ld, int32_t k, const int64_t* part_offsets);
+int32_t   pap_run(const float* S, int64_t n, int64_t ld, int32_t k, const int64_t* part_offsets,
+                  const ap_params* params, float* R, float* A, int32_t* idx, pap_result* out,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch configuration of the ap_iterate sweep, and its autotuner.
  *
  * A cluster of `cluster` CTAs spans one row; each CTA owns a slice of the

@@ -40,8 +40,9 @@ def merge_blocks(n: int, offsets, blocks) -> np.ndarray:
     return Ap
 
 
-def run(S, offsets, lam=0.5, max_iter=200, convits=15):
-    """Algorithm 2 with the given block offsets.
+def run(S, offsets, lam=0.5, max_iter=200, convits=15, fixed_iters=None):
+    """Algorithm 2 with the given block offsets.  With ``fixed_iters`` every
+    run (Step 2 and Step 4) takes exactly that many iterations.
 
     Returns dict(sub=[per-block run dicts], A_prime, final=run dict of Step 4)."""
     S = np.asarray(S, dtype=np.float64)
@@ -49,7 +50,7 @@ def run(S, offsets, lam=0.5, max_iter=200, convits=15):
     subs = []
     for j in range(len(offsets) - 1):
         lo, hi = int(offsets[j]), int(offsets[j + 1])
-        subs.append(ap.run(S[lo:hi, lo:hi], lam, max_iter, convits))
+        subs.append(ap.run(S[lo:hi, lo:hi], lam, max_iter, convits, fixed_iters=fixed_iters))
     Ap = merge_blocks(n, offsets, [s["A"] for s in subs])
-    final = ap.run(S, lam, max_iter, convits, R0=np.zeros((n, n)), A0=Ap)
+    final = ap.run(S, lam, max_iter, convits, R0=np.zeros((n, n)), A0=Ap, fixed_iters=fixed_iters)
     return dict(sub=subs, A_prime=Ap, final=final)

@@ -51,6 +51,18 @@ class ApSweepConfig(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class PapResult(C.Structure):
+    _fields_ = [("k", C.c_int32), ("sub_iters_max", C.c_int32), ("sub_iters_sum", C.c_int64),
+                ("sub_not_converged", C.c_int32), ("pad", C.c_int32), ("sub_ms", C.c_double),
+                ("merge_ms", C.c_double), ("final_ms", C.c_double), ("exemplars_ms", C.c_double),
+                ("final", ApResult)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "final")}
+        d["final"] = self.final.as_dict()
+        return d
+
+
 class ApgbError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -71,6 +83,12 @@ _SIGNATURES = {
     "ap_iterate_workspace_size": (_SZ, [_I64, _I64]),
     "ap_iterate": (C.c_int32, [_P, _P, _P, _I64, _I64, C.POINTER(ApParams), _P,
                                C.POINTER(ApResult), _P, _SZ, _P]),
+    "ap_iterate_batched_workspace_size": (_SZ, [_P, _P, C.c_int32]),
+    "ap_iterate_batched": (C.c_int32, [_P, _P, _P, _P, _P, _P, C.c_int32, C.POINTER(ApParams), _P,
+                                       _P, _P, _SZ, _P]),
+    "pap_run_workspace_size": (_SZ, [_I64, _I64, C.c_int32, _P]),
+    "pap_run": (C.c_int32, [_P, _I64, _I64, C.c_int32, _P, C.POINTER(ApParams), _P, _P, _P,
+                            C.POINTER(PapResult), _P, _SZ, _P]),
     "ap_sweep_get_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_set_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_autotune_workspace_size": (_SZ, [_I64, _I64]),
@@ -223,6 +241,57 @@ def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check
                           C.byref(res), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _check("ap_iterate", st)
     return R, A, res.as_dict(), dec
+
+
+def _i64_array(v):
+    v = [int(x) for x in v]
+    return (C.c_int64 * len(v))(*v)
+
+
+def ap_iterate_batched(S, R, A, offsets, n, ld, damping=0.5, max_iter=200, conv_iter=15,
+                       check_every=0, decisions=False, stream=None):
+    """Algorithm 1 on several problems stored in 1-D float32 arenas (CUDA
+    tensors).  Problem b: n[b] x n[b] at element offset offsets[b], leading
+    dimension ld[b].  Returns (list of result dicts, decisions or None)."""
+    for t, nm in ((S, "S"), (R, "R"), (A, "A")):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{nm} must be a contiguous float32 CUDA tensor")
+    count = len(n)
+    off_a, n_a, ld_a = _i64_array(offsets), _i64_array(n), _i64_array(ld)
+    dec = torch.empty(sum(int(x) for x in n), dtype=torch.int32, device=S.device) if decisions else None
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    out = (ApResult * count)()
+    ws = workspace(lib().ap_iterate_batched_workspace_size(C.cast(n_a, C.c_void_p),
+                                                           C.cast(ld_a, C.c_void_p), count), S.device)
+    st = lib().ap_iterate_batched(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
+                                  C.c_void_p(A.data_ptr()), C.cast(off_a, C.c_void_p),
+                                  C.cast(n_a, C.c_void_p), C.cast(ld_a, C.c_void_p), count,
+                                  C.byref(p), C.c_void_p(dec.data_ptr()) if dec is not None else None,
+                                  C.cast(out, C.c_void_p), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                  _stream(stream))
+    _check("ap_iterate_batched", st)
+    return [o.as_dict() for o in out], dec
+
+
+def pap_run(S, k, part_offsets=None, damping=0.5, max_iter=200, conv_iter=15, check_every=0,
+            R=None, A=None, stream=None):
+    """Algorithm 2 on S (n x n).  Returns (R, A, idx, result dict)."""
+    _dev_f32(S, "S")
+    n = S.shape[0]
+    R = empty_square(n, S.device) if R is None else R
+    A = empty_square(n, S.device) if A is None else A
+    idx = torch.empty(n, dtype=torch.int32, device=S.device)
+    part = _i64_array(part_offsets) if part_offsets is not None else None
+    partp = C.cast(part, C.c_void_p) if part is not None else None
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    res = PapResult()
+    ws = workspace(lib().pap_run_workspace_size(n, S.stride(0), int(k), partp), S.device)
+    st = lib().pap_run(C.c_void_p(S.data_ptr()), n, S.stride(0), int(k), partp, C.byref(p),
+                       C.c_void_p(R.data_ptr()), C.c_void_p(A.data_ptr()),
+                       C.c_void_p(idx.data_ptr()), C.byref(res), C.c_void_p(ws.data_ptr()),
+                       ws.numel(), _stream(stream))
+    _check("pap_run", st)
+    return R, A, idx, res.as_dict()
 
 
 def ap_sweep_get_config(n):

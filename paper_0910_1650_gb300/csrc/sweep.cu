@@ -55,6 +55,8 @@ struct SweepState {
     int32_t pad[4];
 };
 
+// One problem of a launch (a launch sweeps a table of independent problems;
+// a single matrix is a table of one).
 struct SweepArgs {
     const float* S;
     float*       R0;       // caller's R (buffer 0)
@@ -64,9 +66,11 @@ struct SweepArgs {
     int          n;
     int          n4;       // float4 columns spanning n
     int          w4;       // float4 columns per CTA
-    int          ns;       // pipeline stages
-    float        lam;
-    uint32_t     spin_limit;
+    int          cluster_begin;   // first cluster of the grid assigned to this problem
+    int          G;        // clusters assigned to this problem
+    int          ns;       // pipeline stages (launch-wide)
+    float        lam;      // launch-wide
+    uint32_t     spin_limit;      // launch-wide
     const float* cvec;     // r(k,k) + colp(k) of R_{t-1}
     const float* colp;     // colp(k) of R_{t-1}
     float*       pcol;     // [clusters][n] partial column sums of R_t
@@ -75,6 +79,21 @@ struct SweepArgs {
     int32_t*     dec;      // decisions (may be null)
     SweepState*  st;
 };
+
+struct SweepLaunch {
+    const SweepArgs* table;   // device, sorted by cluster_begin
+    int count;
+};
+
+// The problem whose clusters include global cluster `gc` (binary search).
+__device__ __forceinline__ int find_instance(const SweepLaunch& L, int gc) {
+    int lo = 0, hi = L.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.table[mid].cluster_begin <= gc) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // A CTA's partial row result, exchanged across the cluster (20 bytes sent).
 struct __align__(16) Slot {
@@ -113,13 +132,15 @@ __device__ __forceinline__ void set_lane(float4& v, int e, float x) {
 // no cluster-wide barrier (and no fence over outstanding global stores) sits
 // on the per-row path.
 template <int EPT>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(512) sweep_kernel(SweepLaunch L) {
     extern __shared__ __align__(128) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int csize = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
-    const int g = blockIdx.x / csize;
-    const int G = gridDim.x / csize;
+    const int gc = blockIdx.x / csize;
+    const SweepArgs a = L.table[find_instance(L, gc)];
+    const int g = gc - a.cluster_begin;
+    const int G = a.G;
     const int T = blockDim.x;
     const int tid = threadIdx.x;
     const int wid = tid >> 5, lid = tid & 31;
@@ -390,16 +411,17 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     if (csize > 1) cluster.sync();
 }
 
-// Column sums in a fixed cluster order, then the stop rule (block 0).
-__global__ void finalize_kernel(const float* __restrict__ pcol, int G, int n,
-                                const float* __restrict__ rkk, float* colp,
-                                float* cvec, SweepState* st) {
+// Column sums in a fixed cluster order, then the stop rule (block 0 of each
+// problem).  Grid: (column blocks, problems).
+__global__ void finalize_kernel(const SweepArgs* __restrict__ table) {
+    const SweepArgs& a = table[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) {
+    SweepState* st = a.st;
+    if (k < a.n) {
         float s = 0.f;
-        for (int g = 0; g < G; ++g) s += pcol[(int64_t)g * n + k];
-        colp[k] = s;
-        cvec[k] = rkk[k] + s;
+        for (int g = 0; g < a.G; ++g) s += a.pcol[(int64_t)g * a.n + k];
+        const_cast<float*>(a.colp)[k] = s;
+        const_cast<float*>(a.cvec)[k] = a.rkk[k] + s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (st->done) return;
@@ -425,27 +447,27 @@ __global__ void finalize_kernel(const float* __restrict__ pcol, int G, int n,
     }
 }
 
-__global__ void sweep_init_kernel(SweepState* st, int32_t* eflag, int n,
-                                  int max_iter, int conv_iter) {
+__global__ void sweep_init_kernel(const SweepArgs* __restrict__ table, int max_iter, int conv_iter) {
+    const SweepArgs& a = table[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) eflag[k] = 0;
+    if (k < a.n) a.eflag[k] = 0;
     if (k == 0) {
         SweepState s{};
         s.t = 1;
         s.max_iter = max_iter;
         s.conv_iter = conv_iter;
-        *st = s;
+        *a.st = s;
     }
 }
 
-__global__ void nonfinite_kernel(const float* __restrict__ S, int n, int64_t ld,
-                                 int32_t* count) {
+__global__ void nonfinite_kernel(const SweepArgs* __restrict__ table) {
+    const SweepArgs& a = table[blockIdx.y];
     int local = 0;
-    for (int i = blockIdx.x; i < n; i += gridDim.x)
-        for (int k = threadIdx.x; k < n; k += blockDim.x)
-            if (!isfinite(S[(int64_t)i * ld + k])) ++local;
+    for (int i = blockIdx.x; i < a.n; i += gridDim.x)
+        for (int k = threadIdx.x; k < a.n; k += blockDim.x)
+            if (!isfinite(a.S[(int64_t)i * a.ld + k])) ++local;
     local = __reduce_add_sync(0xffffffffu, local);
-    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.st->nonfinite, local);
 }
 
 // ---------------------------------------------------------------------------
@@ -564,35 +586,97 @@ struct EventPairs {
     }
 };
 
-struct SweepWs {
-    float* R1;
-    float* pcol;
-    float* colp;
-    float* cvec;
-    float* rkk;
-    int32_t* eflag;
-    SweepState* st;
+// One matrix of a batch, as the caller describes it.
+struct Problem {
+    const float* S;
+    float* R;
+    float* A;
+    int64_t n, ld;
+    int32_t* dec;
 };
 
-static size_t carve_sweep(void* ws, int64_t n, int64_t ld, int G, SweepWs* w) {
-    SweepWs dummy;
-    if (!w) w = &dummy;
+// How a batch is launched: one configuration (chosen for the largest
+// problem) and the grid's clusters split between problems by work (n^2).
+struct Plan {
+    SweepConfig c;
+    std::vector<int> G;
+    int clusters = 0;
+    int nmax = 0;
+};
+
+static int32_t make_plan(const Problem* P, int count, const SweepConfig* forced, Plan* plan) {
+    int64_t nmax = 0;
+    double work = 0.0;
+    for (int b = 0; b < count; ++b) {
+        nmax = std::max(nmax, P[b].n);
+        work += (double)P[b].n * (double)P[b].n;
+    }
+    plan->nmax = (int)nmax;
+    if (forced) plan->c = *forced;
+    else AP_TRY(choose_config((int)nmax, &plan->c));
+    const int resident = std::max(plan->c.G, 1);
+    plan->G.resize(count);
+    plan->clusters = 0;
+    for (int b = 0; b < count; ++b) {
+        const double share = (double)P[b].n * (double)P[b].n / work;
+        int g = (int)std::lround(share * resident);
+        g = std::max(1, std::min<int>(g, (int)P[b].n));
+        if (count == 1) g = std::max(1, std::min<int>(resident, (int)P[b].n));
+        plan->G[b] = g;
+        plan->clusters += g;
+    }
+    return AP_OK;
+}
+
+struct SweepWs {
+    SweepArgs* table;
+    std::vector<SweepArgs> host;
+};
+
+// Workspace: the problem table, then per problem the second R buffer, the
+// per-cluster column partials, colp, c = r(k,k)+colp, r(k,k), exemplar flags
+// and the stop state.
+static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& plan, SweepWs* w) {
     Carver cv(ws);
-    w->R1 = cv.take<float>((size_t)n * ld);
-    w->pcol = cv.take<float>((size_t)G * n);
-    w->colp = cv.take<float>(n);
-    w->cvec = cv.take<float>(n);
-    w->rkk = cv.take<float>(n);
-    w->eflag = cv.take<int32_t>(n);
-    w->st = cv.take<SweepState>(1);
+    SweepArgs* table = cv.take<SweepArgs>(count);
+    if (w) {
+        w->table = table;
+        w->host.assign(count, SweepArgs{});
+    }
+    int cb = 0;
+    for (int b = 0; b < count; ++b) {
+        const int64_t n = P[b].n, ld = P[b].ld;
+        SweepArgs a{};
+        a.S = P[b].S;
+        a.R0 = P[b].R;
+        a.A = P[b].A;
+        a.ld = ld;
+        a.n = (int)n;
+        a.n4 = (int)((n + 3) / 4);
+        a.w4 = (a.n4 + plan.c.C - 1) / plan.c.C;
+        a.cluster_begin = cb;
+        a.G = plan.G[b];
+        a.ns = plan.c.NS;
+        a.spin_limit = 1u << 20;
+        a.R1 = cv.take<float>((size_t)n * ld);
+        a.pcol = cv.take<float>((size_t)a.G * n);
+        a.colp = cv.take<float>(n);
+        a.cvec = cv.take<float>(n);
+        a.rkk = cv.take<float>(n);
+        a.eflag = cv.take<int32_t>(n);
+        a.st = cv.take<SweepState>(1);
+        a.dec = P[b].dec;
+        cb += a.G;
+        if (w) w->host[b] = a;
+    }
     return cv.used;
 }
 
-static int32_t launch_sweep(const SweepConfig& c, const SweepArgs& args, cudaStream_t s) {
+static int32_t launch_sweep(const SweepConfig& c, int clusters, const SweepLaunch& L, cudaStream_t s) {
     AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)c.smem));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c.C * c.G, 1, 1);
+    cfg.gridDim = dim3(c.C * clusters, 1, 1);
     cfg.blockDim = dim3(c.T, 1, 1);
     cfg.dynamicSmemBytes = c.smem;
     cfg.stream = s;
@@ -605,92 +689,91 @@ static int32_t launch_sweep(const SweepConfig& c, const SweepArgs& args, cudaStr
     cfg.numAttrs = 1;
     cudaError_t e;
     switch (c.EPT) {
-        case 1: e = cudaLaunchKernelEx(&cfg, sweep_kernel<1>, args); break;
-        case 2: e = cudaLaunchKernelEx(&cfg, sweep_kernel<2>, args); break;
-        case 3: e = cudaLaunchKernelEx(&cfg, sweep_kernel<3>, args); break;
-        default: e = cudaLaunchKernelEx(&cfg, sweep_kernel<4>, args); break;
+        case 1: e = cudaLaunchKernelEx(&cfg, sweep_kernel<1>, L); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, sweep_kernel<2>, L); break;
+        case 3: e = cudaLaunchKernelEx(&cfg, sweep_kernel<3>, L); break;
+        default: e = cudaLaunchKernelEx(&cfg, sweep_kernel<4>, L); break;
     }
     return e == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
-int32_t sweep_workspace(int64_t n, int64_t ld, size_t* bytes, SweepConfig* cfg_out) {
-    if (n < 1 || n > INT_MAX / 4 || ld < n) return AP_ERR_INVALID_ARG;
-    SweepConfig c;
-    AP_TRY(choose_config((int)n, &c));
-    SweepWs w;
-    *bytes = carve_sweep(nullptr, n, ld, c.G, &w);
-    if (cfg_out) *cfg_out = c;
-    return AP_OK;
+static bool valid_problem(const Problem& p) {
+    return p.S && p.R && p.A && p.n >= 2 && p.n <= INT_MAX / 4 && p.ld >= p.n && !(p.ld & 3) &&
+           aligned16(p.S) && aligned16(p.R) && aligned16(p.A);
 }
 
-// The iteration loop of ap_iterate for a given launch configuration.
-static int32_t run_sweep(const float* S, float* R, float* A, int64_t n, int64_t ld,
-                         const ap_params* p, int32_t* decisions, ap_result* out, void* ws,
-                         size_t ws_bytes, cudaStream_t s, const SweepConfig& c) {
-    AP_TRY(check_ws(ws, ws_bytes, carve_sweep(nullptr, n, ld, c.G, nullptr)));
-    SweepWs w;
-    carve_sweep(ws, n, ld, c.G, &w);
-    const int ni = (int)n;
+static bool valid_params(const ap_params* p) {
+    return p && p->damping >= 0.f && p->damping < 1.f && p->max_iter >= 1 && p->conv_iter >= 0;
+}
 
-    sweep_init_kernel<<<(ni + 255) / 256, 256, 0, s>>>(w.st, w.eflag, ni, p->max_iter, p->conv_iter);
-    nonfinite_kernel<<<1024, 256, 0, s>>>(S, ni, ld, &w.st->nonfinite);
+// Runs Algorithm 1 on every problem of the batch until each has stopped.
+// out[b] receives problem b's result; sweep timing is per launch (shared).
+static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_result* out,
+                         void* ws, size_t ws_bytes, cudaStream_t s, const Plan& plan) {
+    SweepWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_sweep(nullptr, P, count, plan, nullptr)));
+    carve_sweep(ws, P, count, plan, &w);
+    const SweepConfig& c = plan.c;
+    for (auto& a : w.host) a.lam = p->damping;
+    AP_CUDA_TRY(cudaMemcpyAsync(w.table, w.host.data(), sizeof(SweepArgs) * count,
+                                cudaMemcpyHostToDevice, s));
+    const int nmax = plan.nmax;
+    const dim3 col_grid((nmax + 255) / 256, count);
+    sweep_init_kernel<<<col_grid, 256, 0, s>>>(w.table, p->max_iter, p->conv_iter);
+    nonfinite_kernel<<<dim3(std::min(nmax, 1024), count), 256, 0, s>>>(w.table);
     note_launches(2);
     AP_TRY(last_error());
-    SweepState hs;
-    AP_CUDA_TRY(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    AP_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hs.nonfinite) return AP_ERR_NONFINITE;
-
-    SweepArgs args;
-    args.S = S;
-    args.R0 = R;
-    args.R1 = w.R1;
-    args.A = A;
-    args.ld = ld;
-    args.n = ni;
-    args.n4 = (ni + 3) / 4;
-    args.w4 = c.W4;
-    args.ns = c.NS;
-    args.spin_limit = 1u << 20;
-    args.lam = p->damping;
-    args.cvec = w.cvec;
-    args.colp = w.colp;
-    args.pcol = w.pcol;
-    args.rkk = w.rkk;
-    args.eflag = w.eflag;
-    args.dec = decisions;
-    args.st = w.st;
+    std::vector<SweepState> hs(count);
+    auto read_states = [&]() -> int32_t {
+        for (int b = 0; b < count; ++b)
+            AP_CUDA_TRY(cudaMemcpyAsync(&hs[b], w.host[b].st, sizeof(SweepState),
+                                        cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaStreamSynchronize(s));
+        return AP_OK;
+    };
+    AP_TRY(read_states());
+    for (int b = 0; b < count; ++b)
+        if (hs[b].nonfinite) return AP_ERR_NONFINITE;
 
     // iterations per host check: about 4 ms of sweeping at full bandwidth
+    double elems = 0.0;
+    for (int b = 0; b < count; ++b) elems += (double)P[b].n * (double)P[b].n;
     int chunk = p->check_every;
     if (chunk <= 0) {
-        const double t_iter = 20.0 * (double)n * (double)n / 6.0e12 + 6e-6;
+        const double t_iter = 20.0 * elems / 6.0e12 + 6e-6;
         chunk = (int)std::min(64.0, std::max(1.0, 4e-3 / t_iter));
     }
     const int64_t total = (int64_t)p->max_iter + 1;
     const bool timed = (p->flags & AP_FLAG_TIME_SWEEP) != 0;
     EventPairs ev;
     if (timed) AP_TRY(ev.reserve(chunk));
+    SweepLaunch L{w.table, count};
     int64_t launched = 0;
     int32_t worked = 0;
     double sweep_ms = 0.0;
-    const int fin_blocks = (ni + 255) / 256;
     int32_t t_before = 1;
+    bool all_done = false;
     while (launched < total) {
         const int64_t m = std::min<int64_t>(chunk, total - launched);
         for (int64_t j = 0; j < m; ++j) {
             if (timed) AP_CUDA_TRY(cudaEventRecord(ev.start[j], s));
-            AP_TRY(launch_sweep(c, args, s));
+            AP_TRY(launch_sweep(c, plan.clusters, L, s));
             if (timed) AP_CUDA_TRY(cudaEventRecord(ev.stop[j], s));
-            finalize_kernel<<<fin_blocks, 256, 0, s>>>(w.pcol, c.G, ni, w.rkk, w.colp, w.cvec, w.st);
+            finalize_kernel<<<col_grid, 256, 0, s>>>(w.table);
         }
         note_launches(2 * (uint64_t)m);
         AP_TRY(last_error());
         launched += m;
-        AP_CUDA_TRY(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-        AP_CUDA_TRY(cudaStreamSynchronize(s));
-        const int32_t did = hs.t - t_before;       // launches in this chunk that did work
-        t_before = hs.t;
+        AP_TRY(read_states());
+        int32_t tmax = 1;
+        all_done = true;
+        for (int b = 0; b < count; ++b) {
+            if (hs[b].error) return AP_ERR_TIMEOUT;
+            tmax = std::max(tmax, hs[b].t);
+            all_done = all_done && hs[b].done;
+        }
+        const int32_t did = tmax - t_before;      // launches of this chunk that did work
+        t_before = tmax;
         worked += did;
         if (timed) {
             for (int32_t j = 0; j < did; ++j) {
@@ -699,24 +782,29 @@ static int32_t run_sweep(const float* S, float* R, float* A, int64_t n, int64_t 
                 sweep_ms += ms;
             }
         }
-        if (hs.error) return AP_ERR_TIMEOUT;
-        if (hs.done) break;
+        if (all_done) break;
     }
-    if (!hs.done) return AP_ERR_CUDA;   // cannot happen: launch max_iter+1 always stops
-    if (hs.final_buf == 1)
-        AP_CUDA_TRY(cudaMemcpy2DAsync(R, ld * sizeof(float), w.R1, ld * sizeof(float),
-                                      n * sizeof(float), n, cudaMemcpyDeviceToDevice, s));
+    if (!all_done) return AP_ERR_CUDA;   // cannot happen: launch max_iter+1 always stops
+    int32_t worst = AP_OK;
+    for (int b = 0; b < count; ++b) {
+        const Problem& q = P[b];
+        if (hs[b].final_buf == 1)
+            AP_CUDA_TRY(cudaMemcpy2DAsync(q.R, q.ld * sizeof(float), w.host[b].R1,
+                                          q.ld * sizeof(float), q.n * sizeof(float), q.n,
+                                          cudaMemcpyDeviceToDevice, s));
+        const int32_t status = (p->conv_iter > 0 && !hs[b].converged) ? AP_NOT_CONVERGED : AP_OK;
+        worst = std::max(worst, status);
+        if (out) {
+            out[b] = ap_result{};
+            out[b].iters = hs[b].iters;
+            out[b].converged = hs[b].converged;
+            out[b].status = status;
+            out[b].sweep_ms = sweep_ms;
+            out[b].sweep_launches = worked;
+        }
+    }
     AP_CUDA_TRY(cudaStreamSynchronize(s));
-    const int32_t status = (p->conv_iter > 0 && !hs.converged) ? AP_NOT_CONVERGED : AP_OK;
-    if (out) {
-        *out = ap_result{};
-        out->iters = hs.iters;
-        out->converged = hs.converged;
-        out->status = status;
-        out->sweep_ms = sweep_ms;
-        out->sweep_launches = worked;
-    }
-    return status;
+    return worst;
 }
 
 static void fill_public(const SweepConfig& c, ap_sweep_config* o) {
@@ -728,9 +816,33 @@ static void fill_public(const SweepConfig& c, ap_sweep_config* o) {
     o->smem_bytes = (int32_t)c.smem;
 }
 
-static bool valid_iterate_args(const float* S, float* R, float* A, int64_t n, int64_t ld) {
-    return S && R && A && n >= 2 && n <= INT_MAX / 4 && ld >= n && !(ld & 3) && aligned16(S) &&
-           aligned16(R) && aligned16(A);
+int32_t sweep_workspace(int64_t n, int64_t ld, size_t* bytes) {
+    Problem q{nullptr, nullptr, nullptr, n, ld, nullptr};
+    if (n < 2 || n > INT_MAX / 4 || ld < n) return AP_ERR_INVALID_ARG;
+    Plan plan;
+    AP_TRY(make_plan(&q, 1, nullptr, &plan));
+    *bytes = carve_sweep(nullptr, &q, 1, plan, nullptr);
+    return AP_OK;
+}
+
+static int32_t gather_problems(const float* S, float* R, float* A, const int64_t* off,
+                               const int64_t* n, const int64_t* ld, int32_t count, int32_t* dec,
+                               std::vector<Problem>* P) {
+    if (!S || !R || !A || !off || !n || !ld || count < 1) return AP_ERR_INVALID_ARG;
+    P->resize(count);
+    int64_t doff = 0;
+    for (int b = 0; b < count; ++b) {
+        Problem& q = (*P)[b];
+        q.S = S + off[b];
+        q.R = R + off[b];
+        q.A = A + off[b];
+        q.n = n[b];
+        q.ld = ld[b];
+        q.dec = dec ? dec + doff : nullptr;
+        doff += n[b];
+        if (off[b] < 0 || !valid_problem(q)) return AP_ERR_INVALID_ARG;
+    }
+    return AP_OK;
 }
 
 }  // namespace apgb
@@ -739,22 +851,46 @@ using namespace apgb;
 
 APGB_API size_t ap_iterate_workspace_size(int64_t n, int64_t ld) {
     size_t b = 0;
-    if (sweep_workspace(n, ld, &b, nullptr) != AP_OK) return 0;
+    if (sweep_workspace(n, ld, &b) != AP_OK) return 0;
     return b;
 }
 
 APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
                             const ap_params* p, int32_t* decisions, ap_result* out,
                             void* ws, size_t ws_bytes, void* stream) {
-    if (!p || !valid_iterate_args(S, R, A, n, ld)) return AP_ERR_INVALID_ARG;
-    if (!(p->damping >= 0.f && p->damping < 1.f) || p->max_iter < 1 || p->conv_iter < 0)
-        return AP_ERR_INVALID_ARG;
+    Problem q{S, R, A, n, ld, decisions};
+    if (!valid_params(p) || !valid_problem(q)) return AP_ERR_INVALID_ARG;
     AP_TRY(require_sm103());
-    SweepConfig c;
-    size_t need = 0;
-    AP_TRY(sweep_workspace(n, ld, &need, &c));
-    return run_sweep(S, R, A, n, ld, p, decisions, out, ws, ws_bytes,
-                     static_cast<cudaStream_t>(stream), c);
+    Plan plan;
+    AP_TRY(make_plan(&q, 1, nullptr, &plan));
+    return run_batch(&q, 1, p, out, ws, ws_bytes, static_cast<cudaStream_t>(stream), plan);
+}
+
+APGB_API size_t ap_iterate_batched_workspace_size(const int64_t* n, const int64_t* ld,
+                                                  int32_t count) {
+    if (!n || !ld || count < 1) return 0;
+    if (require_sm103() != AP_OK) return 0;
+    std::vector<Problem> P(count);
+    for (int b = 0; b < count; ++b) {
+        P[b] = Problem{nullptr, nullptr, nullptr, n[b], ld[b], nullptr};
+        if (n[b] < 2 || n[b] > INT_MAX / 4 || ld[b] < n[b]) return 0;
+    }
+    Plan plan;
+    if (make_plan(P.data(), count, nullptr, &plan) != AP_OK) return 0;
+    return carve_sweep(nullptr, P.data(), count, plan, nullptr);
+}
+
+APGB_API int32_t ap_iterate_batched(const float* S, float* R, float* A, const int64_t* offsets,
+                                    const int64_t* n, const int64_t* ld, int32_t count,
+                                    const ap_params* p, int32_t* decisions, ap_result* out,
+                                    void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_params(p)) return AP_ERR_INVALID_ARG;
+    std::vector<Problem> P;
+    AP_TRY(gather_problems(S, R, A, offsets, n, ld, count, decisions, &P));
+    AP_TRY(require_sm103());
+    Plan plan;
+    AP_TRY(make_plan(P.data(), count, nullptr, &plan));
+    return run_batch(P.data(), count, p, out, ws, ws_bytes, static_cast<cudaStream_t>(stream), plan);
 }
 
 APGB_API int32_t ap_sweep_get_config(int64_t n, ap_sweep_config* out) {
@@ -794,9 +930,12 @@ static void for_each_candidate(int n, const std::function<void(const SweepConfig
 APGB_API size_t ap_sweep_autotune_workspace_size(int64_t n, int64_t ld) {
     if (n < 2 || n > INT_MAX / 4 || ld < n) return 0;
     if (require_sm103() != AP_OK) return 0;
+    Problem q{nullptr, nullptr, nullptr, n, ld, nullptr};
     size_t best = 0;
     for_each_candidate((int)n, [&](const SweepConfig& c) {
-        best = std::max(best, carve_sweep(nullptr, n, ld, c.G, nullptr));
+        Plan plan;
+        if (make_plan(&q, 1, &c, &plan) == AP_OK)
+            best = std::max(best, carve_sweep(nullptr, &q, 1, plan, nullptr));
     });
     return best;
 }
@@ -804,8 +943,8 @@ APGB_API size_t ap_sweep_autotune_workspace_size(int64_t n, int64_t ld) {
 APGB_API int32_t ap_sweep_autotune(const float* S, float* R, float* A, int64_t n, int64_t ld,
                                    float damping, int32_t iters, ap_sweep_config* best,
                                    void* ws, size_t ws_bytes, void* stream) {
-    if (!best || !valid_iterate_args(S, R, A, n, ld) || iters < 1 ||
-        !(damping >= 0.f && damping < 1.f))
+    Problem q{S, R, A, n, ld, nullptr};
+    if (!best || !valid_problem(q) || iters < 1 || !(damping >= 0.f && damping < 1.f))
         return AP_ERR_INVALID_ARG;
     AP_TRY(require_sm103());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -818,10 +957,11 @@ APGB_API int32_t ap_sweep_autotune(const float* S, float* R, float* A, int64_t n
     for (const SweepConfig& c : cands) {
         AP_CUDA_TRY(cudaMemset2DAsync(R, ld * sizeof(float), 0, n * sizeof(float), n, s));
         AP_CUDA_TRY(cudaMemset2DAsync(A, ld * sizeof(float), 0, n * sizeof(float), n, s));
+        Plan plan;
+        AP_TRY(make_plan(&q, 1, &c, &plan));
         ap_result r;
-        const int32_t st = run_sweep(S, R, A, n, ld, &p, nullptr, &r, ws, ws_bytes, s, c);
+        const int32_t st = run_batch(&q, 1, &p, &r, ws, ws_bytes, s, plan);
         if (st < 0) return st;
-        // the first and last launches do half the work: time the middle ones
         const double per = r.sweep_ms / std::max(1, r.sweep_launches);
         if (per < best_ms) {
             best_ms = per;
