@@ -205,6 +205,44 @@ int32_t   pap_run(const float* S, int64_t n, int64_t ld, int32_t k, const int64_
                   void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * lap_run -- landmark affinity propagation, Algorithm 3 (Section 4), Steps 1
+ * and 2 (nearest-exemplar embedding without the max_distance gate).
+ *  Step 1: L landmarks chosen by `mode`:
+ *    AP_LANDMARK_UNIFORM  the L points with the smallest splitmix64 keys
+ *                         key(i) = output i+1 of `seed` (ties by index),
+ *                         i.e. a uniform random sample, in ascending order;
+ *    AP_LANDMARK_SCORE    the L largest score[i] (device float[n], ties by
+ *                         index), in ascending index order;
+ *    AP_LANDMARK_GIVEN    landmarks[0..L) (device int32, distinct indices).
+ *  then Algorithm 1 on the landmarks' S (ap_similarity with `precision`,
+ *  preference = its off-diagonal median) -> c exemplars.
+ *  Step 2: every point i gets idx[i] = the exemplar e minimising
+ *  |x_i - e|^2 (bf16 tensor-core GEMM of the centred features, fp32
+ *  accumulate, arg-max of 2 x.e - |e|^2 fused, lowest exemplar on ties);
+ *  exemplars keep themselves.  dpsim = sum over non-exemplars of
+ *  -|x_i - x_idx(i)|^2 and expref = c * preference, in float64.
+ *  X device float32 [n x ldx]; idx device int32 [n]; landmarks_out device
+ *  int32 [L] or NULL.  Synchronous.
+ * ------------------------------------------------------------------------- */
+#define AP_LANDMARK_UNIFORM 0
+#define AP_LANDMARK_SCORE   1
+#define AP_LANDMARK_GIVEN   2
+typedef struct lap_result {
+    int32_t   n_landmarks, n_exemplars;
+    float     pref;                 /* preference of the landmark problem    */
+    int32_t   pad;
+    double    dpsim, expref, netsim;             /* over all n points       */
+    double    select_ms, landmark_ms, assign_ms, netsim_ms;  /* device time */
+    ap_result landmark;             /* Algorithm 1 on the landmarks          */
+} lap_result;
+size_t    lap_run_workspace_size(int64_t n, int64_t d, int64_t n_landmarks);
+int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_landmarks,
+                  int32_t mode, const float* score, const int32_t* landmarks, uint64_t seed,
+                  int32_t precision, const ap_params* params, int32_t* idx,
+                  int32_t* landmarks_out, lap_result* out, void* ws, size_t ws_bytes,
+                  void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch configuration of the ap_iterate sweep, and its autotuner.
  *
  * A cluster of `cluster` CTAs spans one row; each CTA owns a slice of the

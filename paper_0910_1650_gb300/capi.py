@@ -23,6 +23,7 @@ AP_NO_EXEMPLARS = 2
 AP_PREC_FP32, AP_PREC_BF16 = 0, 1
 AP_PREF_MEDIAN, AP_PREF_SCALAR, AP_PREF_VECTOR = 0, 1, 2
 AP_FLAG_TIME_SWEEP = 1
+AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
 AP_NOALLOC_MAX_N = 65536
 
@@ -63,6 +64,18 @@ class PapResult(C.Structure):
         return d
 
 
+class LapResult(C.Structure):
+    _fields_ = [("n_landmarks", C.c_int32), ("n_exemplars", C.c_int32), ("pref", C.c_float),
+                ("pad", C.c_int32), ("dpsim", C.c_double), ("expref", C.c_double),
+                ("netsim", C.c_double), ("select_ms", C.c_double), ("landmark_ms", C.c_double),
+                ("assign_ms", C.c_double), ("netsim_ms", C.c_double), ("landmark", ApResult)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "landmark")}
+        d["landmark"] = self.landmark.as_dict()
+        return d
+
+
 class ApgbError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -89,6 +102,9 @@ _SIGNATURES = {
     "pap_run_workspace_size": (_SZ, [_I64, _I64, C.c_int32, _P]),
     "pap_run": (C.c_int32, [_P, _I64, _I64, C.c_int32, _P, C.POINTER(ApParams), _P, _P, _P,
                             C.POINTER(PapResult), _P, _SZ, _P]),
+    "lap_run_workspace_size": (_SZ, [_I64, _I64, _I64]),
+    "lap_run": (C.c_int32, [_P, _I64, _I64, _I64, _I64, C.c_int32, _P, _P, C.c_uint64, C.c_int32,
+                            C.POINTER(ApParams), _P, _P, C.POINTER(LapResult), _P, _SZ, _P]),
     "ap_sweep_get_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_set_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_autotune_workspace_size": (_SZ, [_I64, _I64]),
@@ -292,6 +308,36 @@ def pap_run(S, k, part_offsets=None, damping=0.5, max_iter=200, conv_iter=15, ch
                        ws.numel(), _stream(stream))
     _check("pap_run", st)
     return R, A, idx, res.as_dict()
+
+
+def lap_run(X, n_landmarks, mode="uniform", score=None, landmarks=None, seed=0, precision="fp32",
+            damping=0.5, max_iter=200, conv_iter=15, check_every=0, stream=None):
+    """Algorithm 3 Steps 1-2 on features X (n x d).  Returns (idx, landmarks,
+    result dict)."""
+    _dev_f32(X, "X")
+    n, d = X.shape
+    L = int(n_landmarks)
+    m = {"uniform": AP_LANDMARK_UNIFORM, "score": AP_LANDMARK_SCORE, "given": AP_LANDMARK_GIVEN}[mode]
+    sc = None
+    if m == AP_LANDMARK_SCORE:
+        sc = score.to(device=X.device, dtype=torch.float32).contiguous()
+    lm_in = None
+    if m == AP_LANDMARK_GIVEN:
+        lm_in = landmarks.to(device=X.device, dtype=torch.int32).contiguous()
+    idx = torch.empty(n, dtype=torch.int32, device=X.device)
+    lm = torch.empty(L, dtype=torch.int32, device=X.device)
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    res = LapResult()
+    ws = workspace(lib().lap_run_workspace_size(n, d, L), X.device)
+    prec = {"fp32": AP_PREC_FP32, "bf16": AP_PREC_BF16}[precision]
+    st = lib().lap_run(C.c_void_p(X.data_ptr()), n, d, X.stride(0), L, m,
+                       C.c_void_p(sc.data_ptr()) if sc is not None else None,
+                       C.c_void_p(lm_in.data_ptr()) if lm_in is not None else None,
+                       int(seed) & 0xFFFFFFFFFFFFFFFF, prec, C.byref(p),
+                       C.c_void_p(idx.data_ptr()), C.c_void_p(lm.data_ptr()), C.byref(res),
+                       C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    _check("lap_run", st)
+    return idx, lm, res.as_dict()
 
 
 def ap_sweep_get_config(n):

@@ -1,0 +1,478 @@
+// lap_run: landmark affinity propagation, Algorithm 3 (Section 4), Steps 1-2.
+//   Step 1: a sample M of landmarks -- uniform (the L points with the smallest
+//           splitmix64 keys), by a caller-supplied score (the L largest), or
+//           given -- then Algorithm 1 on S_M (preference: its off-diagonal
+//           median) -> c exemplars.
+//   Step 2: every point joins its nearest exemplar (squared Euclidean
+//           distance), by the tcgen05 GEMM with the row arg-max fused into its
+//           epilogue; exemplars keep themselves.  netsim over all N points in
+//           float64.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace apgb {
+
+int32_t exemplars_impl(const float* S, const float* R, const float* A, int64_t n, int64_t ld,
+                       int32_t* idx, ap_result* out, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t exemplars_ws_bytes(int64_t n);
+int32_t tc_assign_argmax(const __nv_bfloat16* A, int na, const __nv_bfloat16* B, int nb,
+                         const float* bnrm, int dpad, int32_t* arg, float* best, int32_t* err,
+                         cudaStream_t s);
+
+// ---- landmark keys and exact selection of the L smallest -------------------------
+__global__ void keys_uniform_kernel(uint64_t seed, int64_t n, uint64_t* keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = splitmix64_at(seed, (uint64_t)i + 1);
+}
+
+// Larger score first: key = (order-reversed float key) in the high 32 bits.
+__global__ void keys_score_kernel(const float* __restrict__ score, int64_t n, uint64_t* keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = __float_as_uint(score[i]);
+        const uint32_t fk = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        keys[i] = (uint64_t)(0xFFFFFFFFu - fk) << 32;
+    }
+}
+
+struct KSelect {
+    uint64_t prefix;      // known high digits of the L-th smallest key
+    uint64_t rank;        // its rank among keys sharing the prefix
+    int32_t shift;
+    int32_t pad;
+    uint64_t less;        // keys strictly below the threshold (after the last pass)
+};
+
+__global__ void kselect_init_kernel(KSelect* st, uint64_t rank, unsigned* hist) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+    if (threadIdx.x == 0) {
+        st->prefix = 0;
+        st->rank = rank;
+        st->shift = 56;
+        st->less = 0;
+    }
+}
+
+__global__ void kselect_hist_kernel(const uint64_t* __restrict__ keys, int64_t n,
+                                    const KSelect* __restrict__ st, unsigned* hist) {
+    __shared__ unsigned h[256];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const int shift = st->shift;
+    const uint64_t mask = (shift >= 56) ? 0ull : (~0ull << (shift + 8));
+    const uint64_t pre = st->prefix;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        if ((k & mask) == pre) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+__global__ void kselect_scan_kernel(KSelect* st, unsigned* hist) {
+    if (threadIdx.x != 0) return;
+    uint64_t r = st->rank;
+    int b = 0;
+    for (; b < 256; ++b) {
+        if (r < hist[b]) break;
+        r -= hist[b];
+        st->less += hist[b];
+    }
+    if (b > 255) b = 255;            // unreachable with consistent counts
+    st->prefix |= (uint64_t)b << st->shift;
+    st->rank = r;
+    st->shift -= 8;
+    for (int x = 0; x < 256; ++x) hist[x] = 0;
+}
+
+// Single block, index order: keys below the threshold, then as many keys
+// equal to it as are needed (lowest indices first).  out is ascending.
+__global__ void kselect_compact_kernel(const uint64_t* __restrict__ keys, int64_t n,
+                                       const KSelect* __restrict__ st, int64_t L, int32_t* out) {
+    __shared__ int wsum[32], weq[32];
+    __shared__ int64_t base;
+    __shared__ int64_t ties_left;
+    const uint64_t thr = st->prefix;
+    if (threadIdx.x == 0) {
+        base = 0;
+        ties_left = L - (int64_t)st->less;
+    }
+    __syncthreads();
+    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t lo = 0; lo < n; lo += blockDim.x) {
+        const int64_t i = lo + threadIdx.x;
+        const uint64_t k = (i < n) ? keys[i] : ~0ull;
+        const bool lt = i < n && k < thr;
+        const bool eq = i < n && k == thr;
+        const unsigned blt = __ballot_sync(0xffffffffu, lt), beq = __ballot_sync(0xffffffffu, eq);
+        if (lid == 0) { wsum[wid] = __popc(blt); weq[wid] = __popc(beq); }
+        __syncthreads();
+        int before_lt = 0, before_eq = 0;
+        for (int w = 0; w < wid; ++w) { before_lt += wsum[w]; before_eq += weq[w]; }
+        const int my_eq = before_eq + __popc(beq & ((1u << lid) - 1u));
+        const bool take_eq = eq && my_eq < ties_left;
+        // slots before this thread: all lt and taken eq of lower indices
+        int taken_eq_before = 0;
+        for (int w = 0; w < wid; ++w) taken_eq_before += weq[w];
+        {
+            const int64_t cand = (int64_t)taken_eq_before + __popc(beq & ((1u << lid) - 1u));
+            taken_eq_before = (int)(cand < ties_left ? cand : ties_left);
+        }
+        const int64_t pos = base + before_lt + __popc(blt & ((1u << lid) - 1u)) + taken_eq_before;
+        if (lt || take_eq) out[pos] = (int32_t)i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tl = 0, te = 0;
+            for (int w = 0; w < nw; ++w) { tl += wsum[w]; te += weq[w]; }
+            const int64_t te_taken = te < ties_left ? (int64_t)te : ties_left;
+            base += tl + te_taken;
+            ties_left -= te_taken;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- gathers, centring, labels, netsim -------------------------------------------
+__global__ void gather_rows_kernel(const float* __restrict__ X, int64_t ldx, int d,
+                                   const int32_t* __restrict__ rows, int64_t m, float* out) {
+    for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+        const float* src = X + (int64_t)rows[r] * ldx;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) out[r * d + j] = src[j];
+    }
+}
+
+__global__ void colsum_rows_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ldx,
+                                   int rows_per_block, double* part) {
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = (r0 + rows_per_block < n) ? r0 + rows_per_block : n;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t i = r0; i < r1; ++i) s += (double)X[i * ldx + j];
+        part[(int64_t)blockIdx.x * d + j] = s;
+    }
+}
+
+__global__ void colmean_rows_kernel(const double* __restrict__ part, int nb, int d, int64_t n,
+                                    float* mean) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * d + j];
+    mean[j] = (float)(s / (double)n);
+}
+
+// bf16 of (x - mean) for the listed rows (or rows 0..m-1), zero padded to
+// [mpad x dpad]; optional fp32 squared norms of the rounded rows.
+__global__ void centre_bf16_kernel(const float* __restrict__ X, int64_t ldx, int d,
+                                   const int32_t* __restrict__ rows, int64_t m, int64_t mpad,
+                                   int dpad, const float* __restrict__ mean, __nv_bfloat16* out,
+                                   float* nrm) {
+    const int warps = blockDim.x >> 5, lid = threadIdx.x & 31;
+    for (int64_t r = blockIdx.x * (int64_t)warps + (threadIdx.x >> 5); r < mpad;
+         r += (int64_t)gridDim.x * warps) {
+        float acc = 0.f;
+        const int64_t src_row = (r < m) ? (rows ? rows[r] : r) : -1;
+        for (int j = lid; j < dpad; j += 32) {
+            float v = 0.f;
+            if (src_row >= 0 && j < d) v = X[src_row * ldx + j] - mean[j];
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            out[r * dpad + j] = b;
+            const float bv = __bfloat162float(b);
+            acc = fmaf(bv, bv, acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (nrm && lid == 0) nrm[r] = acc;
+    }
+}
+
+// Exemplars of the landmark problem: E = {j : idx_L(j) == j}, as landmark
+// positions in ascending order, and their point indices.
+__global__ void landmark_exemplars_kernel(const int32_t* __restrict__ idxL, int64_t L,
+                                          const int32_t* __restrict__ lm, int32_t* epts,
+                                          int32_t* count) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t lo = 0; lo < L; lo += blockDim.x) {
+        const int64_t j = lo + threadIdx.x;
+        const bool f = j < L && idxL[j] == (int32_t)j;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lid == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < wid; ++w) before += wsum[w];
+        if (f) epts[base + before + __popc(bal & ((1u << lid) - 1u))] = lm[j];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += wsum[w];
+            base += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+__global__ void labels_kernel(const int32_t* __restrict__ arg, int64_t n,
+                              const int32_t* __restrict__ epts, int32_t* idx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        idx[i] = epts[arg[i]];
+}
+
+__global__ void exemplars_keep_self_kernel(const int32_t* __restrict__ epts, int c, int32_t* idx) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < c) idx[epts[j]] = epts[j];
+}
+
+// dp[i] = -|x_i - x_idx(i)|^2 in float64 (0 for exemplars), one warp per row.
+__global__ void lap_dpsim_kernel(const float* __restrict__ X, int64_t ldx, int d, int64_t n,
+                                 const int32_t* __restrict__ idx, double* dp) {
+    const int warps = blockDim.x >> 5, lid = threadIdx.x & 31;
+    for (int64_t i = blockIdx.x * (int64_t)warps + (threadIdx.x >> 5); i < n;
+         i += (int64_t)gridDim.x * warps) {
+        const int64_t c = idx[i];
+        double s = 0.0;
+        if (c != i)
+            for (int j = lid; j < d; j += 32) {
+                const double t = (double)X[i * ldx + j] - (double)X[c * ldx + j];
+                s += t * t;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lid == 0) dp[i] = -s;
+    }
+}
+
+// Fixed-order float64 sum (one block).
+__global__ void sum_f64_kernel(const double* __restrict__ v, int64_t n, double* out) {
+    __shared__ double sh[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = threadIdx.x * per, hi = (lo + per < n) ? lo + per : n;
+    double x = 0.0;
+    for (int64_t i = lo; i < hi; ++i) x += v[i];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// ---- workspace ------------------------------------------------------------------------
+struct LapWs {
+    uint64_t* keys;
+    KSelect* ks;
+    unsigned* hist;
+    int32_t* lm;
+    float* XL;
+    float *SL, *RL, *AL;
+    int32_t* idxL;
+    void* sub_ws;
+    size_t sub_bytes;
+    int32_t* epts;
+    int32_t* ecount;
+    double* part;
+    float* mean;
+    __nv_bfloat16* Xb;
+    __nv_bfloat16* Eb;
+    float* enrm;
+    int32_t* arg;
+    double* dp;
+    double* sums;
+    int32_t* err;
+};
+
+static int64_t ld32(int64_t n) { return (n + 31) / 32 * 32; }
+
+static size_t carve_lap(void* ws, int64_t n, int64_t d, int64_t L, LapWs* w) {
+    const int dpad = (int)((d + 63) / 64 * 64);
+    const int64_t ldL = ld32(L);
+    const size_t sub = std::max({ap_similarity_workspace_size(L, d), ap_iterate_workspace_size(L, ldL),
+                                 exemplars_ws_bytes(L)});
+    const int64_t npad = (n + 127) / 128 * 128;
+    const int64_t cpad = (L + 255) / 256 * 256;        // at most L exemplars
+    const int nb = (int)((n + 4095) / 4096);
+    Carver c(ws);
+    w->keys = c.take<uint64_t>(n);
+    w->ks = c.take<KSelect>(1);
+    w->hist = c.take<unsigned>(256);
+    w->lm = c.take<int32_t>(L);
+    w->XL = c.take<float>((size_t)L * d);
+    w->SL = c.take<float>((size_t)L * ldL);
+    w->RL = c.take<float>((size_t)L * ldL);
+    w->AL = c.take<float>((size_t)L * ldL);
+    w->idxL = c.take<int32_t>(L);
+    w->sub_ws = c.take<char>(sub);
+    w->sub_bytes = sub;
+    w->epts = c.take<int32_t>(L);
+    w->ecount = c.take<int32_t>(1);
+    w->part = c.take<double>((size_t)nb * d);
+    w->mean = c.take<float>(d);
+    w->Xb = c.take<__nv_bfloat16>((size_t)npad * dpad);
+    w->Eb = c.take<__nv_bfloat16>((size_t)cpad * dpad);
+    w->enrm = c.take<float>(cpad);
+    w->arg = c.take<int32_t>(n);
+    w->dp = c.take<double>(n);
+    w->sums = c.take<double>(2);
+    w->err = c.take<int32_t>(1);
+    return c.used;
+}
+
+static int32_t select_smallest(const uint64_t* keys, int64_t n, int64_t L, KSelect* ks,
+                               unsigned* hist, int32_t* out, cudaStream_t s) {
+    kselect_init_kernel<<<1, 256, 0, s>>>(ks, (uint64_t)(L - 1), hist);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 2048);
+    for (int p = 0; p < 8; ++p) {
+        kselect_hist_kernel<<<grid, 256, 0, s>>>(keys, n, ks, hist);
+        kselect_scan_kernel<<<1, 32, 0, s>>>(ks, hist);
+    }
+    kselect_compact_kernel<<<1, 1024, 0, s>>>(keys, n, ks, L, out);
+    note_launches(18);
+    return last_error();
+}
+
+}  // namespace apgb
+
+using namespace apgb;
+
+APGB_API size_t lap_run_workspace_size(int64_t n, int64_t d, int64_t n_landmarks) {
+    if (n < 2 || d < 1 || n_landmarks < 2 || n_landmarks > n || n > INT_MAX / 2 || d > 65536)
+        return 0;
+    LapWs w;
+    return carve_lap(nullptr, n, d, n_landmarks, &w);
+}
+
+APGB_API int32_t lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t L,
+                         int32_t mode, const float* score, const int32_t* landmarks,
+                         uint64_t seed, int32_t precision, const ap_params* params, int32_t* idx,
+                         int32_t* landmarks_out, lap_result* out, void* ws, size_t ws_bytes,
+                         void* stream) {
+    if (!X || !idx || !out || !params || n < 2 || d < 1 || ldx < d || L < 2 || L > n ||
+        n > INT_MAX / 2 || d > 65536)
+        return AP_ERR_INVALID_ARG;
+    if (mode == AP_LANDMARK_SCORE && !score) return AP_ERR_INVALID_ARG;
+    if (mode == AP_LANDMARK_GIVEN && !landmarks) return AP_ERR_INVALID_ARG;
+    if (mode != AP_LANDMARK_UNIFORM && mode != AP_LANDMARK_SCORE && mode != AP_LANDMARK_GIVEN)
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LapWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_lap(nullptr, n, d, L, &w)));
+    carve_lap(ws, n, d, L, &w);
+    const int di = (int)d;
+    const int dpad = (di + 63) / 64 * 64;
+    const int64_t ldL = ld32(L);
+
+    cudaEvent_t ev[5];
+    for (auto& e : ev) AP_CUDA_TRY(cudaEventCreate(&e));
+    struct Guard {
+        cudaEvent_t* e;
+        ~Guard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); }
+    } guard{ev};
+    AP_CUDA_TRY(cudaEventRecord(ev[0], s));
+
+    // ---- Step 1: landmarks ----
+    const int kgrid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    if (mode == AP_LANDMARK_GIVEN) {
+        AP_CUDA_TRY(cudaMemcpyAsync(w.lm, landmarks, sizeof(int32_t) * L, cudaMemcpyDeviceToDevice, s));
+    } else {
+        if (mode == AP_LANDMARK_UNIFORM) keys_uniform_kernel<<<kgrid, 256, 0, s>>>(seed, n, w.keys);
+        else keys_score_kernel<<<kgrid, 256, 0, s>>>(score, n, w.keys);
+        note_launches(1);
+        AP_TRY(select_smallest(w.keys, n, L, w.ks, w.hist, w.lm, s));
+    }
+    if (landmarks_out)
+        AP_CUDA_TRY(cudaMemcpyAsync(landmarks_out, w.lm, sizeof(int32_t) * L, cudaMemcpyDeviceToDevice, s));
+    gather_rows_kernel<<<(int)std::min<int64_t>(L, 65535), 128, 0, s>>>(X, ldx, di, w.lm, L, w.XL);
+    note_launches(1);
+    AP_TRY(last_error());
+    AP_CUDA_TRY(cudaEventRecord(ev[1], s));
+
+    // ---- Step 1: Algorithm 1 on the landmarks ----
+    float pref = 0.f;
+    AP_TRY(ap_similarity(w.XL, L, d, d, w.SL, ldL, precision, AP_PREF_MEDIAN, nullptr, 0.0, 0,
+                         &pref, w.sub_ws, w.sub_bytes, stream));
+    AP_CUDA_TRY(cudaMemset2DAsync(w.RL, ldL * sizeof(float), 0, L * sizeof(float), L, s));
+    AP_CUDA_TRY(cudaMemset2DAsync(w.AL, ldL * sizeof(float), 0, L * sizeof(float), L, s));
+    ap_result lr;
+    const int32_t st_it = ap_iterate(w.SL, w.RL, w.AL, L, ldL, params, nullptr, &lr, w.sub_ws,
+                                     w.sub_bytes, stream);
+    if (st_it < 0) return st_it;
+    const int32_t li = lr.iters, lc = lr.converged;
+    const int32_t st_ex = exemplars_impl(w.SL, w.RL, w.AL, L, ldL, w.idxL, &lr, w.sub_ws,
+                                         w.sub_bytes, s);
+    if (st_ex < 0) return st_ex;
+    lr.iters = li;
+    lr.converged = lc;
+    AP_CUDA_TRY(cudaEventRecord(ev[2], s));
+    *out = lap_result{};
+    out->n_landmarks = (int32_t)L;
+    out->landmark = lr;
+    out->pref = pref;
+    if (st_ex == AP_NO_EXEMPLARS) {
+        AP_CUDA_TRY(cudaMemsetAsync(idx, 0xFF, sizeof(int32_t) * n, s));
+        AP_CUDA_TRY(cudaStreamSynchronize(s));
+        out->n_exemplars = 0;
+        out->dpsim = out->expref = out->netsim = NAN;
+        return AP_NO_EXEMPLARS;
+    }
+
+    // ---- Step 2: nearest exemplar for every point (tensor cores) ----
+    landmark_exemplars_kernel<<<1, 1024, 0, s>>>(w.idxL, L, w.lm, w.epts, w.ecount);
+    int32_t c = 0;
+    AP_CUDA_TRY(cudaMemcpyAsync(&c, w.ecount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    const int nb = (int)((n + 4095) / 4096);
+    colsum_rows_kernel<<<nb, 128, 0, s>>>(X, n, di, ldx, 4096, w.part);
+    colmean_rows_kernel<<<(di + 127) / 128, 128, 0, s>>>(w.part, nb, di, n, w.mean);
+    const int64_t npad = (n + 127) / 128 * 128;
+    const int64_t cpad = ((int64_t)c + 255) / 256 * 256;
+    centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, nullptr, n, npad, dpad, w.mean, w.Xb, nullptr);
+    centre_bf16_kernel<<<(int)std::min<int64_t>((cpad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, w.epts, c, cpad, dpad, w.mean, w.Eb, w.enrm);
+    AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+    note_launches(5);
+    AP_TRY(last_error());
+    AP_TRY(tc_assign_argmax(w.Xb, (int)n, w.Eb, c, w.enrm, dpad, w.arg, nullptr, w.err, s));
+    const int lgrid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    labels_kernel<<<lgrid, 256, 0, s>>>(w.arg, n, w.epts, idx);
+    exemplars_keep_self_kernel<<<(c + 255) / 256, 256, 0, s>>>(w.epts, c, idx);
+    AP_CUDA_TRY(cudaEventRecord(ev[3], s));
+    lap_dpsim_kernel<<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, s>>>(X, ldx, di, n, idx,
+                                                                                   w.dp);
+    sum_f64_kernel<<<1, 1024, 0, s>>>(w.dp, n, w.sums);
+    note_launches(4);
+    AP_TRY(last_error());
+    AP_CUDA_TRY(cudaEventRecord(ev[4], s));
+    double dps = 0.0;
+    int32_t err = 0;
+    AP_CUDA_TRY(cudaMemcpyAsync(&dps, w.sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return AP_ERR_TIMEOUT;
+    float ms[4];
+    for (int i = 0; i < 4; ++i) AP_CUDA_TRY(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+    out->select_ms = ms[0];
+    out->landmark_ms = ms[1];
+    out->assign_ms = ms[2];
+    out->netsim_ms = ms[3];
+    out->n_exemplars = c;
+    out->dpsim = dps;
+    out->expref = (double)pref * c;
+    out->netsim = out->dpsim + out->expref;
+    return (params->conv_iter > 0 && !lc) ? AP_NOT_CONVERGED : AP_OK;
+}
