@@ -243,6 +243,70 @@ int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_l
                   void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned warm start.  The paper has no learned part: this network plays the
+ * role of Algorithm 2's merged availabilities (a warm start for Algorithm 1)
+ * and its exemplar score can choose Algorithm 3's landmarks (the non-uniform
+ * landmark selection Section 4 leaves to future work).
+ *
+ * Features of point k (APL_IN = 19): the 16 largest off-diagonal s(k,j) in
+ * decreasing order, the mean and standard deviation of the off-diagonal
+ * s(k,j), and s(k,k), all divided by `scale` (> 0, e.g. |median preference|).
+ * Network 19 -> 256 -> 256 -> 3 with ReLU; outputs (r_hat, a_hat, logit):
+ * predicted converged r(k,k)/scale, a(k,k)/scale and exemplar log-odds.
+ * The input is first standardised, x -> (x - mu) * isd, with mu and isd
+ * fixed (set by the caller from training features; their gradient is zero).
+ * Parameters: one flat float32 vector of apl_param_count() entries (W1 256x19,
+ * b1, W2 256x256, b2, W3 3x256, b3, mu 19, isd 19, row-major), plus a bf16
+ * copy (same offsets) that the products use with fp32 accumulation.
+ * Training loss (mean over rows): (r_hat - t_r)^2 + (a_hat - t_a)^2 +
+ * softplus(logit) - t_e * logit; Adam (0.9, 0.999, 1e-8, bias-corrected).
+ * All device pointers are caller-owned; rows-sized scratch comes from `ws`
+ * (apl_workspace_size(rows) bytes).  The calls below enqueue work only.
+ * ------------------------------------------------------------------------- */
+#define APL_IN  19
+#define APL_HID 256
+#define APL_OUT 3
+int64_t   apl_param_count(void);
+int32_t   apl_features(const float* S, int64_t n, int64_t ld, float scale, float* F /*n x 19*/,
+                       void* stream);
+int32_t   apl_targets(const float* R, const float* A, const int32_t* decisions, int64_t n,
+                      int64_t ld, float scale, float* T /*n x 3*/, void* stream);
+size_t    apl_workspace_size(int64_t rows);
+int32_t   apl_sync_bf16(const float* P, void* P16, void* stream);
+int32_t   apl_forward(const float* P, const void* P16, const float* F, int64_t rows,
+                      float* Y /*rows x 3*/, void* ws, size_t ws_bytes, void* stream);
+/* One Adam step on a batch: forward, loss (device float, may be NULL),
+ * backward, update of P, M, V (moments) and the bf16 copy.  step >= 1.
+ * grad (device float[apl_param_count()] or NULL) receives the gradient. */
+int32_t   apl_train_step(float* P, void* P16, float* M, float* V, int64_t step, float lr,
+                         const float* F, const float* T, int64_t rows, float* loss, float* grad,
+                         void* ws, size_t ws_bytes, void* stream);
+/* R <- 0; A <- the column-constant availabilities of the predictions: at a
+ * fixed point of Eq. 3-4, a(k,k) = colp(k) and a(i,k) = min(0, r(k,k) +
+ * colp(k)) up to the i-th term, so A(i,k) = min(0, (r_hat_k + a_hat_k) *
+ * scale) for i != k and A(k,k) = max(0, a_hat_k * scale). */
+int32_t   apl_warm_start(const float* Y, int64_t n, float scale, float* R, float* A, int64_t ld,
+                         void* stream);
+
+/* apl_ap_run: features -> network -> warm start -> Algorithm 1 -> outputs.
+ * With judge != 0 it also runs Algorithm 1 from R = A = 0 (the method without
+ * the network) and keeps the warm result only if its net similarity is within
+ * 0.5 % of the cold one; otherwise R, A, idx and out->result are the cold
+ * run's.  Synchronous. */
+typedef struct apl_result {
+    int32_t   used_warm;
+    int32_t   warm_iters, cold_iters;
+    int32_t   pad;
+    double    warm_netsim, cold_netsim;
+    double    features_ms, forward_ms, warm_ms, cold_ms;   /* device time    */
+    ap_result result;
+} apl_result;
+size_t    apl_ap_run_workspace_size(int64_t n, int64_t ld);
+int32_t   apl_ap_run(const float* S, int64_t n, int64_t ld, const float* P, const void* P16,
+                     float scale, const ap_params* params, int32_t judge, float* R, float* A,
+                     int32_t* idx, apl_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch configuration of the ap_iterate sweep, and its autotuner.
  *
  * A cluster of `cluster` CTAs spans one row; each CTA owns a slice of the

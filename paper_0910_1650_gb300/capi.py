@@ -76,6 +76,18 @@ class LapResult(C.Structure):
         return d
 
 
+class AplResult(C.Structure):
+    _fields_ = [("used_warm", C.c_int32), ("warm_iters", C.c_int32), ("cold_iters", C.c_int32),
+                ("pad", C.c_int32), ("warm_netsim", C.c_double), ("cold_netsim", C.c_double),
+                ("features_ms", C.c_double), ("forward_ms", C.c_double), ("warm_ms", C.c_double),
+                ("cold_ms", C.c_double), ("result", ApResult)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "result")}
+        d["result"] = self.result.as_dict()
+        return d
+
+
 class ApgbError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -105,6 +117,18 @@ _SIGNATURES = {
     "lap_run_workspace_size": (_SZ, [_I64, _I64, _I64]),
     "lap_run": (C.c_int32, [_P, _I64, _I64, _I64, _I64, C.c_int32, _P, _P, C.c_uint64, C.c_int32,
                             C.POINTER(ApParams), _P, _P, C.POINTER(LapResult), _P, _SZ, _P]),
+    "apl_param_count": (C.c_int64, []),
+    "apl_features": (C.c_int32, [_P, _I64, _I64, C.c_float, _P, _P]),
+    "apl_targets": (C.c_int32, [_P, _P, _P, _I64, _I64, C.c_float, _P, _P]),
+    "apl_workspace_size": (_SZ, [_I64]),
+    "apl_sync_bf16": (C.c_int32, [_P, _P, _P]),
+    "apl_forward": (C.c_int32, [_P, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "apl_train_step": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_float, _P, _P, _I64, _P, _P,
+                                   _P, _SZ, _P]),
+    "apl_warm_start": (C.c_int32, [_P, _I64, C.c_float, _P, _P, _I64, _P]),
+    "apl_ap_run_workspace_size": (_SZ, [_I64, _I64]),
+    "apl_ap_run": (C.c_int32, [_P, _I64, _I64, _P, _P, C.c_float, C.POINTER(ApParams), C.c_int32,
+                               _P, _P, _P, C.POINTER(AplResult), _P, _SZ, _P]),
     "ap_sweep_get_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_set_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_autotune_workspace_size": (_SZ, [_I64, _I64]),
@@ -404,3 +428,82 @@ def ap_exemplars_noalloc(S, R, A, idx=None, stream=None):
                                     C.c_void_p(idx.data_ptr()), C.byref(res), _stream(stream))
     _check("ap_exemplars_noalloc", st)
     return idx, res.as_dict()
+
+
+# ---- learned warm start ----------------------------------------------------------
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def apl_param_count():
+    return int(lib().apl_param_count())
+
+
+def apl_features(S, scale, stream=None):
+    _dev_f32(S, "S")
+    n = S.shape[0]
+    F = torch.empty((n, 19), dtype=torch.float32, device=S.device)
+    _check("apl_features", lib().apl_features(_ptr(S), n, S.stride(0), float(scale), _ptr(F),
+                                              _stream(stream)), ok=(AP_OK,))
+    return F
+
+
+def apl_targets(R, A, decisions, scale, stream=None):
+    n = R.shape[0]
+    T = torch.empty((n, 3), dtype=torch.float32, device=R.device)
+    _check("apl_targets", lib().apl_targets(_ptr(R), _ptr(A), _ptr(decisions), n, R.stride(0),
+                                            float(scale), _ptr(T), _stream(stream)), ok=(AP_OK,))
+    return T
+
+
+def apl_sync_bf16(P, P16, stream=None):
+    _check("apl_sync_bf16", lib().apl_sync_bf16(_ptr(P), _ptr(P16), _stream(stream)), ok=(AP_OK,))
+
+
+def apl_forward(P, P16, F, stream=None):
+    rows = F.shape[0]
+    Y = torch.empty((rows, 3), dtype=torch.float32, device=F.device)
+    ws = workspace(lib().apl_workspace_size(rows), F.device)
+    _check("apl_forward", lib().apl_forward(_ptr(P), _ptr(P16), _ptr(F), rows, _ptr(Y),
+                                            _ptr(ws), ws.numel(), _stream(stream)), ok=(AP_OK,))
+    return Y
+
+
+def apl_train_step(P, P16, M, V, step, lr, F, T, ws=None, want_grad=False, stream=None):
+    """One Adam step in place on (P, P16, M, V).  Returns (loss tensor, grad or None)."""
+    rows = F.shape[0]
+    if ws is None:
+        ws = workspace(lib().apl_workspace_size(rows), F.device)
+    loss = torch.empty(1, dtype=torch.float32, device=F.device)
+    grad = torch.empty(apl_param_count(), dtype=torch.float32, device=F.device) if want_grad else None
+    _check("apl_train_step", lib().apl_train_step(_ptr(P), _ptr(P16), _ptr(M), _ptr(V), int(step),
+                                                  float(lr), _ptr(F), _ptr(T), rows, _ptr(loss),
+                                                  _ptr(grad), _ptr(ws), ws.numel(),
+                                                  _stream(stream)), ok=(AP_OK,))
+    return loss, grad
+
+
+def apl_warm_start(Y, scale, R, A, stream=None):
+    n = Y.shape[0]
+    _check("apl_warm_start", lib().apl_warm_start(_ptr(Y), n, float(scale), _ptr(R), _ptr(A),
+                                                  R.stride(0), _stream(stream)), ok=(AP_OK,))
+
+
+def apl_ap_run(S, P, P16, scale, damping=0.9, max_iter=1000, conv_iter=15, judge=True,
+               check_every=0, stream=None):
+    """Warm-started Algorithm 1 (judged by the cold start).  Returns
+    (R, A, idx, result dict)."""
+    _dev_f32(S, "S")
+    n = S.shape[0]
+    R = empty_square(n, S.device)
+    A = empty_square(n, S.device)
+    idx = torch.empty(n, dtype=torch.int32, device=S.device)
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    res = AplResult()
+    ws = workspace(lib().apl_ap_run_workspace_size(n, S.stride(0)), S.device)
+    st = lib().apl_ap_run(_ptr(S), n, S.stride(0), _ptr(P), _ptr(P16), float(scale), C.byref(p),
+                          1 if judge else 0, _ptr(R), _ptr(A), _ptr(idx), C.byref(res), _ptr(ws),
+                          ws.numel(), _stream(stream))
+    _check("apl_ap_run", st)
+    return R, A, idx, res.as_dict()

@@ -1,0 +1,582 @@
+// The learned warm start (not part of the paper; it plays the role Algorithm
+// 2's merged availabilities play, and its exemplar score can choose
+// Algorithm 3's landmarks).
+//
+// Per point k of S with preference scale p > 0, 19 features: the 16 largest
+// off-diagonal s(k,j) in decreasing order, the mean and standard deviation of
+// the off-diagonal s(k,j), and s(k,k), all divided by p.  A 19-256-256-3
+// network (ReLU) maps them to (r_hat, a_hat, logit): predicted converged
+// r(k,k)/p, a(k,k)/p and the exemplar log-odds.  Training: mean over rows of
+// (r_hat-t_r)^2 + (a_hat-t_a)^2 + softplus(logit) - t_e*logit, Adam.
+//
+// Parameters: one flat fp32 vector (W1 256x19, b1, W2 256x256, b2, W3 3x256,
+// b3, mu 19, isd 19); the input is standardised first, x -> (x - mu) * isd,
+// with mu and isd fixed (their gradient is zero, so Adam leaves them).  The
+// products use a bf16 copy of the weights with fp32 accumulation.  All
+// reductions (loss, weight gradients) run in a fixed order.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace apgb {
+namespace mlp {
+
+constexpr int IN = 19, HID = 256, OUT = 3;
+constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
+                  OFF_B2 = OFF_W2 + HID * HID, OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + OUT * HID,
+                  OFF_MU = OFF_B3 + OUT, OFF_ISD = OFF_MU + IN, NP = OFF_ISD + IN;
+
+// ---- features -------------------------------------------------------------------
+constexpr int TOPK = 16;
+
+__global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, float inv_scale,
+                                float* F) {
+    __shared__ float hv[32];
+    __shared__ int ht[32];
+    __shared__ double s1w[32], s2w[32];
+    const int tid = threadIdx.x, lid = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const float* row = S + (int64_t)k * ld;
+        float top[TOPK];
+#pragma unroll
+        for (int q = 0; q < TOPK; ++q) top[q] = -INFINITY;
+        double s1 = 0.0, s2 = 0.0;
+        for (int j = tid; j < n; j += blockDim.x) {
+            if (j == k) continue;
+            const float v = row[j];
+            s1 += v;
+            s2 += (double)v * v;
+            if (v > top[TOPK - 1]) {            // insertion into the descending list
+                float x = v;
+#pragma unroll
+                for (int q = 0; q < TOPK; ++q) {
+                    if (x > top[q]) { const float t = top[q]; top[q] = x; x = t; }
+                }
+            }
+        }
+        // block sums (fixed order: warp tree, then warps in order)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lid == 0) { s1w[wid] = s1; s2w[wid] = s2; }
+        // 16 rounds of block arg-max over each thread's next candidate
+        int head = 0;
+        float outv[TOPK];
+        for (int r = 0; r < TOPK; ++r) {
+            float v = head < TOPK ? top[head] : -INFINITY;
+            int who = tid;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
+                if (v2 > v || (v2 == v && w2 < who)) { v = v2; who = w2; }
+            }
+            if (lid == 0) { hv[wid] = v; ht[wid] = who; }
+            __syncthreads();
+            float bv = hv[0];
+            int bw = ht[0];
+            for (int w = 1; w < nw; ++w)
+                if (hv[w] > bv || (hv[w] == bv && ht[w] < bw)) { bv = hv[w]; bw = ht[w]; }
+            if (tid == bw) ++head;
+            outv[r] = bv;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int w = 0; w < nw; ++w) { t1 += s1w[w]; t2 += s2w[w]; }
+            const double m = t1 / (double)(n - 1);
+            const double var = fmax(0.0, t2 / (double)(n - 1) - m * m);
+            float* f = F + (int64_t)k * IN;
+            float last = outv[0];
+            for (int r = 0; r < TOPK; ++r) {
+                if (outv[r] == -INFINITY) outv[r] = last;   // fewer than 16 off-diagonal values
+                last = outv[r];
+                f[r] = outv[r] * inv_scale;
+            }
+            f[16] = (float)(m * (double)inv_scale);
+            f[17] = (float)(sqrt(var) * (double)inv_scale);
+            f[18] = row[k] * inv_scale;
+        }
+        __syncthreads();
+    }
+}
+
+// Fn = (F - mu) * isd, row-major [rows x 19].
+__global__ void standardise_kernel(const float* __restrict__ F, int rows,
+                                   const float* __restrict__ P, float* Fn) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * IN) return;
+    const int j = (int)(e % IN);
+    Fn[e] = (F[e] - P[OFF_MU + j]) * P[OFF_ISD + j];
+}
+
+// ---- dense layers ----------------------------------------------------------------
+constexpr int TR = 64, TO = 64, TK = 16;
+
+// Y[r][o] = act(sum_i X[r][i] W[o][i] + b[o]); W bf16 [out x in].
+__global__ void __launch_bounds__(256) linear_fwd_kernel(const float* __restrict__ X, int rows,
+                                                         int in, const __nv_bfloat16* __restrict__ W,
+                                                         const float* __restrict__ b, int out,
+                                                         int relu, float* Y) {
+    __shared__ float xs[TK][TR + 1], ws[TK][TO + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r0 = blockIdx.x * TR, o0 = blockIdx.y * TO;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < in; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TR; e += 256) {
+            const int kk = e % TK, rr = e / TK;
+            const int r = r0 + rr, k = k0 + kk;
+            xs[kk][rr] = (r < rows && k < in) ? X[(int64_t)r * in + k] : 0.f;
+            const int o = o0 + rr;
+            ws[kk][rr] = (o < out && k < in) ? __bfloat162float(W[(int64_t)o * in + k]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    acc[a][c] = fmaf(xs[kk][ty * 4 + a], ws[kk][tx * 4 + c], acc[a][c]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = r0 + ty * 4 + a;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int o = o0 + tx * 4 + c;
+            if (o >= out) continue;
+            float v = acc[a][c] + b[o];
+            if (relu) v = fmaxf(v, 0.f);
+            Y[(int64_t)r * out + o] = v;
+        }
+    }
+}
+
+// dX[r][i] = (sum_o G[r][o] W[o][i]) * (H[r][i] > 0); W bf16 [out x in].
+__global__ void __launch_bounds__(256) linear_bwd_input_kernel(const float* __restrict__ G,
+                                                               int rows, int out,
+                                                               const __nv_bfloat16* __restrict__ W,
+                                                               int in, const float* __restrict__ H,
+                                                               float* dX) {
+    __shared__ float gs[TK][TR + 1], ws[TK][TO + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r0 = blockIdx.x * TR, i0 = blockIdx.y * TO;
+    float acc[4][4] = {};
+    for (int o0 = 0; o0 < out; o0 += TK) {
+        for (int e = threadIdx.x; e < TK * TR; e += 256) {
+            const int oo = e % TK, rr = e / TK;
+            const int r = r0 + rr, o = o0 + oo;
+            gs[oo][rr] = (r < rows && o < out) ? G[(int64_t)r * out + o] : 0.f;
+            const int i = i0 + rr;
+            ws[oo][rr] = (o < out && i < in) ? __bfloat162float(W[(int64_t)o * in + i]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int oo = 0; oo < TK; ++oo)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    acc[a][c] = fmaf(gs[oo][ty * 4 + a], ws[oo][tx * 4 + c], acc[a][c]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = r0 + ty * 4 + a;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + tx * 4 + c;
+            if (i >= in) continue;
+            const int64_t at = (int64_t)r * in + i;
+            dX[at] = H[at] > 0.f ? acc[a][c] : 0.f;
+        }
+    }
+}
+
+// gW[o][i] = sum_r G[r][o] X[r][i] (rows in a fixed order); one output tile
+// per block, so the sum is deterministic.
+__global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restrict__ G, int rows,
+                                                          int out, const float* __restrict__ X,
+                                                          int in, float* gW) {
+    __shared__ float gs[TK][TO + 1], xs[TK][TO + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int o0 = blockIdx.x * TO, i0 = blockIdx.y * TO;
+    float acc[4][4] = {};
+    for (int rr0 = 0; rr0 < rows; rr0 += TK) {
+        for (int e = threadIdx.x; e < TK * TO; e += 256) {
+            const int kk = e / TO, c = e % TO;
+            const int r = rr0 + kk;
+            gs[kk][c] = (r < rows && o0 + c < out) ? G[(int64_t)r * out + o0 + c] : 0.f;
+            xs[kk][c] = (r < rows && i0 + c < in) ? X[(int64_t)r * in + i0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    acc[a][c] = fmaf(gs[kk][ty * 4 + a], xs[kk][tx * 4 + c], acc[a][c]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int o = o0 + ty * 4 + a;
+        if (o >= out) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + tx * 4 + c;
+            if (i < in) gW[(int64_t)o * in + i] = acc[a][c];
+        }
+    }
+}
+
+// gb[o] = sum_r G[r][o], one thread per column, rows in order.
+__global__ void bias_grad_kernel(const float* __restrict__ G, int rows, int out, float* gb) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= out) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += G[(int64_t)r * out + o];
+    gb[o] = s;
+}
+
+// Per-row loss terms and dL/dY (already divided by the row count).
+__global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict__ T, int rows,
+                            float* G, float* lrow) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const float inv = 1.f / (float)rows;
+    const float d = Y[r * 3 + 0] - T[r * 3 + 0];
+    const float e = Y[r * 3 + 1] - T[r * 3 + 1];
+    const float z = Y[r * 3 + 2], t = T[r * 3 + 2];
+    const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));     // softplus(z)
+    lrow[r] = d * d + e * e + sp - t * z;
+    G[r * 3 + 0] = 2.f * d * inv;
+    G[r * 3 + 1] = 2.f * e * inv;
+    G[r * 3 + 2] = (1.f / (1.f + expf(-z)) - t) * inv;
+}
+
+__global__ void mean_kernel(const float* __restrict__ v, int n, float* out) {
+    __shared__ double sh[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(n, lo + per);
+    double x = 0.0;
+    for (int i = lo; i < hi; ++i) x += v[i];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (float)(sh[0] / (double)n);
+}
+
+// Adam with bias correction; refreshes the bf16 copy of the weights.
+__global__ void adam_kernel(float* P, const float* __restrict__ g, float* m, float* v, int64_t np,
+                            float lr, float b1, float b2, float eps, float c1, float c2,
+                            __nv_bfloat16* P16) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float mi = b1 * m[i] + (1.f - b1) * g[i];
+        const float vi = b2 * v[i] + (1.f - b2) * g[i] * g[i];
+        m[i] = mi;
+        v[i] = vi;
+        const float p = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        P[i] = p;
+        P16[i] = __float2bfloat16_rn(p);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ P, int64_t np, __nv_bfloat16* P16) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P16[i] = __float2bfloat16_rn(P[i]);
+}
+
+__global__ void targets_kernel(const float* __restrict__ R, const float* __restrict__ A,
+                               const int32_t* __restrict__ dec, int n, int64_t ld, float inv_scale,
+                               float* T) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    T[k * 3 + 0] = R[(int64_t)k * ld + k] * inv_scale;
+    T[k * 3 + 1] = A[(int64_t)k * ld + k] * inv_scale;
+    T[k * 3 + 2] = dec[k] == k ? 1.f : 0.f;
+}
+
+// Column-constant availabilities from the per-point predictions (the fixed
+// point of Eq. 3-4 up to the i-th term): A(i,k) = min(0, (r_hat_k+a_hat_k)p)
+// for i != k, A(k,k) = max(0, a_hat_k p).  One block-row of A per block.
+__global__ void warm_columns_kernel(const float* __restrict__ Y, int n, float scale, float* A,
+                                    int64_t ld) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        float* row = A + (int64_t)i * ld;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const float rh = Y[k * 3 + 0], ah = Y[k * 3 + 1];
+            row[k] = (k == i) ? fmaxf(0.f, ah * scale) : fminf(0.f, (rh + ah) * scale);
+        }
+    }
+}
+
+struct MlpWs {
+    float *Fn, *H1, *H2, *Y, *G3, *G2, *G1, *lrow, *grad;
+};
+
+static size_t carve(void* ws, int64_t rows, MlpWs* w) {
+    Carver c(ws);
+    w->Fn = c.take<float>((size_t)rows * IN);
+    w->H1 = c.take<float>((size_t)rows * HID);
+    w->H2 = c.take<float>((size_t)rows * HID);
+    w->Y = c.take<float>((size_t)rows * OUT);
+    w->G3 = c.take<float>((size_t)rows * OUT);
+    w->G2 = c.take<float>((size_t)rows * HID);
+    w->G1 = c.take<float>((size_t)rows * HID);
+    w->lrow = c.take<float>(rows);
+    w->grad = c.take<float>(NP);
+    return c.used;
+}
+
+static dim3 grid2(int rows, int cols) { return dim3((rows + TR - 1) / TR, (cols + TO - 1) / TO); }
+
+static int32_t forward(const float* P, const __nv_bfloat16* P16, const float* F, int rows,
+                       const MlpWs& w, float* Y, cudaStream_t s) {
+    standardise_kernel<<<(int)(((int64_t)rows * IN + 255) / 256), 256, 0, s>>>(F, rows, P, w.Fn);
+    linear_fwd_kernel<<<grid2(rows, HID), 256, 0, s>>>(w.Fn, rows, IN, P16 + OFF_W1, P + OFF_B1, HID, 1, w.H1);
+    linear_fwd_kernel<<<grid2(rows, HID), 256, 0, s>>>(w.H1, rows, HID, P16 + OFF_W2, P + OFF_B2, HID, 1, w.H2);
+    linear_fwd_kernel<<<grid2(rows, OUT), 256, 0, s>>>(w.H2, rows, HID, P16 + OFF_W3, P + OFF_B3, OUT, 0, Y);
+    note_launches(4);
+    return last_error();
+}
+
+}  // namespace mlp
+}  // namespace apgb
+
+using namespace apgb;
+using namespace apgb::mlp;
+
+APGB_API int64_t apl_param_count(void) { return NP; }
+
+APGB_API int32_t apl_features(const float* S, int64_t n, int64_t ld, float scale, float* F,
+                              void* stream) {
+    if (!S || !F || n < 2 || ld < n || n > INT_MAX || !(scale > 0.f)) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    features_kernel<<<(int)std::min<int64_t>(n, 65535), 256, 0, s>>>(S, (int)n, ld, 1.f / scale, F);
+    note_launches(1);
+    return last_error();
+}
+
+APGB_API int32_t apl_targets(const float* R, const float* A, const int32_t* dec, int64_t n,
+                             int64_t ld, float scale, float* T, void* stream) {
+    if (!R || !A || !dec || !T || n < 1 || ld < n || n > INT_MAX || !(scale > 0.f))
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    targets_kernel<<<(int)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        R, A, dec, (int)n, ld, 1.f / scale, T);
+    note_launches(1);
+    return last_error();
+}
+
+APGB_API size_t apl_workspace_size(int64_t rows) {
+    if (rows < 1 || rows > INT_MAX / HID) return 0;
+    MlpWs w;
+    return carve(nullptr, rows, &w);
+}
+
+APGB_API int32_t apl_sync_bf16(const float* P, void* P16, void* stream) {
+    if (!P || !P16) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    to_bf16_kernel<<<(int)((NP + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        P, NP, static_cast<__nv_bfloat16*>(P16));
+    note_launches(1);
+    return last_error();
+}
+
+APGB_API int32_t apl_forward(const float* P, const void* P16, const float* F, int64_t rows,
+                             float* Y, void* ws, size_t ws_bytes, void* stream) {
+    if (!P || !P16 || !F || !Y || rows < 1 || rows > INT_MAX / HID) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    MlpWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve(nullptr, rows, &w)));
+    carve(ws, rows, &w);
+    return forward(P, static_cast<const __nv_bfloat16*>(P16), F, (int)rows, w, Y,
+                   static_cast<cudaStream_t>(stream));
+}
+
+APGB_API int32_t apl_train_step(float* P, void* P16, float* M, float* V, int64_t step, float lr,
+                                const float* F, const float* T, int64_t rows, float* loss,
+                                float* grad_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!P || !P16 || !M || !V || !F || !T || rows < 1 || rows > INT_MAX / HID || step < 1 ||
+        !(lr >= 0.f))
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MlpWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve(nullptr, rows, &w)));
+    carve(ws, rows, &w);
+    const int r = (int)rows;
+    const __nv_bfloat16* W16 = static_cast<const __nv_bfloat16*>(P16);
+    AP_TRY(forward(P, W16, F, r, w, w.Y, s));
+    loss_kernel<<<(r + 255) / 256, 256, 0, s>>>(w.Y, T, r, w.G3, w.lrow);
+    if (loss) mean_kernel<<<1, 1024, 0, s>>>(w.lrow, r, loss);
+    float* g = w.grad;
+    // layer 3
+    weight_grad_kernel<<<dim3(1, (HID + TO - 1) / TO), 256, 0, s>>>(w.G3, r, OUT, w.H2, HID, g + OFF_W3);
+    bias_grad_kernel<<<1, 32, 0, s>>>(w.G3, r, OUT, g + OFF_B3);
+    linear_bwd_input_kernel<<<grid2(r, HID), 256, 0, s>>>(w.G3, r, OUT, W16 + OFF_W3, HID, w.H2, w.G2);
+    // layer 2
+    weight_grad_kernel<<<dim3((HID + TO - 1) / TO, (HID + TO - 1) / TO), 256, 0, s>>>(w.G2, r, HID, w.H1, HID, g + OFF_W2);
+    bias_grad_kernel<<<(HID + 255) / 256, 256, 0, s>>>(w.G2, r, HID, g + OFF_B2);
+    linear_bwd_input_kernel<<<grid2(r, HID), 256, 0, s>>>(w.G2, r, HID, W16 + OFF_W2, HID, w.H1, w.G1);
+    // layer 1
+    weight_grad_kernel<<<dim3((HID + TO - 1) / TO, 1), 256, 0, s>>>(w.G1, r, HID, w.Fn, IN, g + OFF_W1);
+    bias_grad_kernel<<<(HID + 255) / 256, 256, 0, s>>>(w.G1, r, HID, g + OFF_B1);
+    AP_CUDA_TRY(cudaMemsetAsync(g + OFF_MU, 0, sizeof(float) * 2 * IN, s));   // fixed standardisation
+    if (grad_out) AP_CUDA_TRY(cudaMemcpyAsync(grad_out, g, sizeof(float) * NP, cudaMemcpyDeviceToDevice, s));
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)step));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)step));
+    adam_kernel<<<(int)((NP + 255) / 256), 256, 0, s>>>(P, g, M, V, NP, lr, b1, b2, 1e-8f, c1, c2,
+                                                        static_cast<__nv_bfloat16*>(P16));
+    note_launches(loss ? 12 : 11);
+    return last_error();
+}
+
+APGB_API int32_t apl_warm_start(const float* Y, int64_t n, float scale, float* R, float* A,
+                                int64_t ld, void* stream) {
+    if (!Y || !R || !A || n < 1 || ld < n || n > INT_MAX || !(scale > 0.f)) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    AP_CUDA_TRY(cudaMemset2DAsync(R, ld * sizeof(float), 0, n * sizeof(float), n, s));
+    warm_columns_kernel<<<(int)std::min<int64_t>(n, 4096), 256, 0, s>>>(Y, (int)n, scale, A, ld);
+    note_launches(1);
+    return last_error();
+}
+
+// ---- warm-started Algorithm 1, judged by the cold start ---------------------------
+namespace apgb {
+int32_t exemplars_impl(const float* S, const float* R, const float* A, int64_t n, int64_t ld,
+                       int32_t* idx, ap_result* out, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t exemplars_ws_bytes(int64_t n);
+
+struct RunWs {
+    float *F, *Y, *R2, *A2;
+    int32_t* idx2;
+    void* mlp_ws;
+    size_t mlp_bytes;
+    void* sub_ws;
+    size_t sub_bytes;
+};
+
+static size_t carve_run(void* ws, int64_t n, int64_t ld, RunWs* w) {
+    const size_t mb = apl_workspace_size(n);
+    const size_t sb = std::max(ap_iterate_workspace_size(n, ld), exemplars_ws_bytes(n));
+    Carver c(ws);
+    w->F = c.take<float>((size_t)n * mlp::IN);
+    w->Y = c.take<float>((size_t)n * mlp::OUT);
+    w->R2 = c.take<float>((size_t)n * ld);
+    w->A2 = c.take<float>((size_t)n * ld);
+    w->idx2 = c.take<int32_t>(n);
+    w->mlp_ws = c.take<char>(mb);
+    w->mlp_bytes = mb;
+    w->sub_ws = c.take<char>(sb);
+    w->sub_bytes = sb;
+    return (mb && sb) ? c.used : 0;
+}
+}  // namespace apgb
+
+APGB_API size_t apl_ap_run_workspace_size(int64_t n, int64_t ld) {
+    if (n < 2 || ld < n || n > INT_MAX / 256) return 0;
+    RunWs w;
+    return carve_run(nullptr, n, ld, &w);
+}
+
+APGB_API int32_t apl_ap_run(const float* S, int64_t n, int64_t ld, const float* P, const void* P16,
+                            float scale, const ap_params* params, int32_t judge, float* R, float* A,
+                            int32_t* idx, apl_result* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!S || !P || !P16 || !params || !R || !A || !idx || !out || n < 2 || ld < n ||
+        n > INT_MAX / 256 || !(scale > 0.f))
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RunWs w;
+    const size_t need = carve_run(nullptr, n, ld, &w);
+    if (need == 0) return AP_ERR_INVALID_ARG;
+    AP_TRY(check_ws(ws, ws_bytes, need));
+    carve_run(ws, n, ld, &w);
+    cudaEvent_t ev[5];
+    for (auto& e : ev) AP_CUDA_TRY(cudaEventCreate(&e));
+    struct Guard {
+        cudaEvent_t* e;
+        ~Guard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); }
+    } guard{ev};
+
+    *out = apl_result{};
+    AP_CUDA_TRY(cudaEventRecord(ev[0], s));
+    AP_TRY(apl_features(S, n, ld, scale, w.F, stream));
+    AP_CUDA_TRY(cudaEventRecord(ev[1], s));
+    AP_TRY(apl_forward(P, P16, w.F, n, w.Y, w.mlp_ws, w.mlp_bytes, stream));
+    AP_TRY(apl_warm_start(w.Y, n, scale, R, A, ld, stream));
+    AP_CUDA_TRY(cudaEventRecord(ev[2], s));
+    ap_result rw;
+    const int32_t sw = ap_iterate(S, R, A, n, ld, params, nullptr, &rw, w.sub_ws, w.sub_bytes, stream);
+    if (sw < 0) return sw;
+    const int32_t wi = rw.iters, wc = rw.converged;
+    const int32_t swe = exemplars_impl(S, R, A, n, ld, idx, &rw, w.sub_ws, w.sub_bytes, s);
+    if (swe < 0) return swe;
+    rw.iters = wi;
+    rw.converged = wc;
+    rw.status = std::max(sw, swe);
+    AP_CUDA_TRY(cudaEventRecord(ev[3], s));
+    out->warm_iters = wi;
+    out->warm_netsim = rw.netsim;
+    out->result = rw;
+    out->used_warm = 1;
+    if (judge) {
+        AP_CUDA_TRY(cudaMemset2DAsync(w.R2, ld * sizeof(float), 0, n * sizeof(float), n, s));
+        AP_CUDA_TRY(cudaMemset2DAsync(w.A2, ld * sizeof(float), 0, n * sizeof(float), n, s));
+        ap_result rc;
+        const int32_t sc = ap_iterate(S, w.R2, w.A2, n, ld, params, nullptr, &rc, w.sub_ws,
+                                      w.sub_bytes, stream);
+        if (sc < 0) return sc;
+        const int32_t ci = rc.iters, cc = rc.converged;
+        const int32_t sce = exemplars_impl(S, w.R2, w.A2, n, ld, w.idx2, &rc, w.sub_ws,
+                                           w.sub_bytes, s);
+        if (sce < 0) return sce;
+        rc.iters = ci;
+        rc.converged = cc;
+        rc.status = std::max(sc, sce);
+        out->cold_iters = ci;
+        out->cold_netsim = rc.netsim;
+        // the judge: keep the warm result only within 0.5 % of the cold net similarity
+        const bool ok = rw.n_exemplars > 0 && rc.n_exemplars > 0 &&
+                        std::fabs(rw.netsim - rc.netsim) <= 0.005 * std::fabs(rc.netsim);
+        if (!ok || rw.n_exemplars == 0) {
+            out->used_warm = 0;
+            out->result = rc;
+            AP_CUDA_TRY(cudaMemcpy2DAsync(R, ld * sizeof(float), w.R2, ld * sizeof(float),
+                                          n * sizeof(float), n, cudaMemcpyDeviceToDevice, s));
+            AP_CUDA_TRY(cudaMemcpy2DAsync(A, ld * sizeof(float), w.A2, ld * sizeof(float),
+                                          n * sizeof(float), n, cudaMemcpyDeviceToDevice, s));
+            AP_CUDA_TRY(cudaMemcpyAsync(idx, w.idx2, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    AP_CUDA_TRY(cudaEventRecord(ev[4], s));
+    AP_CUDA_TRY(cudaEventSynchronize(ev[4]));
+    float ms[4];
+    for (int i = 0; i < 4; ++i) AP_CUDA_TRY(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+    out->features_ms = ms[0];
+    out->forward_ms = ms[1];
+    out->warm_ms = ms[2];
+    out->cold_ms = ms[3];
+    return out->result.status;
+}

@@ -227,3 +227,17 @@ def workload(c: int, scale: float = 1.0):
         n = max(8, int(round(1_000_000 * scale)))
         return gaussian_mixture(n, 128, 1000, config_seed(3), 4.0, 0.5, False)
     raise ValueError(c)
+
+
+def mlp_init(seed: int = SEED_BASE + 77, n_in: int = 19, hid: int = 256, n_out: int = 3):
+    """Initial parameters of the warm-start network as one float32 vector
+    (W1, b1, W2, b2, W3, b3, mu, isd): He-normal weights N(0, 2/fan_in), zero
+    biases, identity input standardisation (mu = 0, isd = 1)."""
+    st = Stream(seed, 200)
+    parts = []
+    for fan_out, fan_in in ((hid, n_in), (hid, hid), (n_out, hid)):
+        parts.append(st.normal(fan_out * fan_in) * np.sqrt(2.0 / fan_in))
+        parts.append(np.zeros(fan_out))
+    parts.append(np.zeros(n_in))
+    parts.append(np.ones(n_in))
+    return np.concatenate(parts).astype(np.float32)
