@@ -131,8 +131,12 @@ __device__ __forceinline__ void set_lane(float4& v, int e, float x) {
 // peer's shared memory with st.async, completing on the peer's mbarrier, so
 // no cluster-wide barrier (and no fence over outstanding global stores) sits
 // on the per-row path.
+// Register ceilings keep two CTAs of up to 320 threads (EPT 2) on an SM.
 template <int EPT>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepLaunch L) {
+struct SweepRegs { static constexpr int value = EPT == 1 ? 64 : EPT == 2 ? 96 : 128; };
+
+template <int EPT>
+__global__ void __launch_bounds__(512) __maxnreg__(SweepRegs<EPT>::value) sweep_kernel(SweepLaunch L) {
     extern __shared__ __align__(128) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int csize = (int)cluster.num_blocks();
@@ -225,10 +229,14 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepLaunch L) {
         float4* R4 = sR(s);
         float4* A4 = sA(s);
         const float colp_i = doA ? a.colp[i] : 0.f;
+        const int fi = i >> 2;                  // the float4 holding column i
         float4 s4[EPT], r4[EPT];
         Top2 tp{-INFINITY, -INFINITY, INT_MAX};
         float dv = -INFINITY;
         int dj = INT_MAX;
+        // Columns reach a thread in increasing order, so inside a thread a
+        // strictly larger value is all an update needs (the first index
+        // stays); index tie-breaks matter only when threads are merged.
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             const int f = f_begin + tid + q * T;
@@ -237,30 +245,55 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepLaunch L) {
                 s4[q] = doR ? S4[x] : make_float4(0.f, 0.f, 0.f, 0.f);
                 r4[q] = R4[x];
                 float4 a4 = A4[x];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = 4 * f + e;
-                    if (k < a.n) {
-                        const float sv = lane(s4[q], e), rv = lane(r4[q], e);
-                        float av = lane(a4, e);
-                        if (doA) {
-                            const float an = (k == i) ? colp_i
-                                                      : fminf(0.f, lane(cv[q], e) - fmaxf(0.f, rv));
-                            av = fmaf(lam, av, oml * an);
-                            set_lane(a4, e, av);
-                            argmax_merge(dv, dj, av + rv, k);
-                        }
-                        if (doR) top2_push(tp, av + sv, k);
-                    }
-                }
-                if (doA) {
-                    if (f < f_full_end) {
+                if (f != fi && f < f_full_end) {
+                    // fast path: no diagonal, no ragged tail
+                    if (doA) {
+                        a4.x = fmaf(lam, a4.x, oml * fminf(0.f, cv[q].x - fmaxf(0.f, r4[q].x)));
+                        a4.y = fmaf(lam, a4.y, oml * fminf(0.f, cv[q].y - fmaxf(0.f, r4[q].y)));
+                        a4.z = fmaf(lam, a4.z, oml * fminf(0.f, cv[q].z - fmaxf(0.f, r4[q].z)));
+                        a4.w = fmaf(lam, a4.w, oml * fminf(0.f, cv[q].w - fmaxf(0.f, r4[q].w)));
+                        const int k0 = 4 * f;
+                        float d;
+                        d = a4.x + r4[q].x; if (d > dv) { dv = d; dj = k0; }
+                        d = a4.y + r4[q].y; if (d > dv) { dv = d; dj = k0 + 1; }
+                        d = a4.z + r4[q].z; if (d > dv) { dv = d; dj = k0 + 2; }
+                        d = a4.w + r4[q].w; if (d > dv) { dv = d; dj = k0 + 3; }
                         A4[x] = a4;
-                    } else {
-                        float* Arow = a.A + (int64_t)i * a.ld;
+                    }
+                    if (doR) {
+                        const int k0 = 4 * f;
+                        float v;
+                        v = a4.x + s4[q].x; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0; }
+                        v = a4.y + s4[q].y; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 1; }
+                        v = a4.z + s4[q].z; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 2; }
+                        v = a4.w + s4[q].w; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 3; }
+                    }
+                } else {
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (4 * f + e < a.n) Arow[4 * f + e] = lane(a4, e);
+                    for (int e = 0; e < 4; ++e) {
+                        const int k = 4 * f + e;
+                        if (k < a.n) {
+                            const float sv = lane(s4[q], e), rv = lane(r4[q], e);
+                            float av = lane(a4, e);
+                            if (doA) {
+                                const float an = (k == i) ? colp_i
+                                                          : fminf(0.f, lane(cv[q], e) - fmaxf(0.f, rv));
+                                av = fmaf(lam, av, oml * an);
+                                set_lane(a4, e, av);
+                                argmax_merge(dv, dj, av + rv, k);
+                            }
+                            if (doR) top2_push(tp, av + sv, k);
+                        }
+                    }
+                    if (doA) {
+                        if (f < f_full_end) {
+                            A4[x] = a4;
+                        } else {
+                            float* Arow = a.A + (int64_t)i * a.ld;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * f + e < a.n) Arow[4 * f + e] = lane(a4, e);
+                        }
                     }
                 }
             }
@@ -336,30 +369,44 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepLaunch L) {
         }
 
         if (doR) {
+            const int fj = j1 >> 2;             // the float4 holding the row's arg-max
 #pragma unroll
             for (int q = 0; q < EPT; ++q) {
                 const int f = f_begin + tid + q * T;
                 if (f < f_end) {
                     float4 o;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int k = 4 * f + e;
-                        const float sv = lane(s4[q], e), rv = lane(r4[q], e);
-                        const float m = (k == j1) ? m2 : m1;
-                        const float rn = fmaf(lam, rv, oml * (sv - m));
-                        set_lane(o, e, rn);
-                        if (k < a.n) {
-                            if (k == i) a.rkk[i] = rn;
-                            else set_lane(acc[q], e, lane(acc[q], e) + fmaxf(0.f, rn));
-                        }
-                    }
-                    if (f < f_full_end) {
+                    if (f != fi && f != fj && f < f_full_end) {
+                        // fast path: every column takes m1, none is the diagonal
+                        o.x = fmaf(lam, r4[q].x, oml * (s4[q].x - m1));
+                        o.y = fmaf(lam, r4[q].y, oml * (s4[q].y - m1));
+                        o.z = fmaf(lam, r4[q].z, oml * (s4[q].z - m1));
+                        o.w = fmaf(lam, r4[q].w, oml * (s4[q].w - m1));
+                        acc[q].x += fmaxf(0.f, o.x);
+                        acc[q].y += fmaxf(0.f, o.y);
+                        acc[q].z += fmaxf(0.f, o.z);
+                        acc[q].w += fmaxf(0.f, o.w);
                         R4[f - f_begin] = o;
                     } else {
-                        float* Orow = Rout + (int64_t)i * a.ld;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (4 * f + e < a.n) Orow[4 * f + e] = lane(o, e);
+                        for (int e = 0; e < 4; ++e) {
+                            const int k = 4 * f + e;
+                            const float sv = lane(s4[q], e), rv = lane(r4[q], e);
+                            const float m = (k == j1) ? m2 : m1;
+                            const float rn = fmaf(lam, rv, oml * (sv - m));
+                            set_lane(o, e, rn);
+                            if (k < a.n) {
+                                if (k == i) a.rkk[i] = rn;
+                                else set_lane(acc[q], e, lane(acc[q], e) + fmaxf(0.f, rn));
+                            }
+                        }
+                        if (f < f_full_end) {
+                            R4[f - f_begin] = o;
+                        } else {
+                            float* Orow = Rout + (int64_t)i * a.ld;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * f + e < a.n) Orow[4 * f + e] = lane(o, e);
+                        }
                     }
                 }
             }
