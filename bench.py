@@ -280,9 +280,103 @@ def run_gpu(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if not args.no_ttc and world == 1:
+            del S, R, A, Xd
+            torch.cuda.empty_cache()
+            line["time_to_converge"] = time_to_converge(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def time_to_converge(dev):
+    """Time to converge of partition AP and landmark AP against plain GPU AP
+    on the same inputs (device time, CUDA events), with net similarities."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ev[0].record()
+        r = fn()
+        ev[1].record()
+        ev[1].synchronize()
+        return r, ev[0].elapsed_time(ev[1])
+
+    # ---- partition AP: 60000 points on 10 subspaces of R^100, 32 uneven subsets
+    X, _ = synth.subspaces()
+    offs = synth.uneven_partition()
+    n = X.shape[0]
+    S, _ = capi.ap_similarity(torch.from_numpy(X).to(dev), precision="bf16")
+    R = capi.empty_square(n, dev, 0.0)
+    A = capi.empty_square(n, dev, 0.0)
+
+    def plain():
+        R.zero_()
+        A.zero_()
+        _, _, r, _ = capi.ap_iterate(S, R, A, damping=DAMPING, max_iter=MAX_ITER,
+                                     conv_iter=CONV_ITER, decisions=False)
+        _, ex = capi.ap_exemplars(S, R, A)
+        return r, ex
+
+    (rp, exp_), t_plain = timed(plain)
+    (_, _, _, pr), t_pap = timed(lambda: capi.pap_run(S, len(offs) - 1, list(offs), damping=DAMPING,
+                                                      max_iter=MAX_ITER, conv_iter=CONV_ITER,
+                                                      R=R, A=A))
+    out["pap"] = {
+        "workload": "60000 points on 10 random 5-dim subspaces of R^100 + N(0,0.01) noise; "
+                    "32 uneven seeded subsets (500-4000)",
+        "plain": {"iters": rp["iters"], "ms": round(t_plain, 1), "netsim": exp_["netsim"],
+                  "n_exemplars": exp_["n_exemplars"]},
+        "pap": {"sub_iters_max": pr["sub_iters_max"], "step4_iters": pr["final"]["iters"],
+                "ms": round(t_pap, 1), "sub_ms": round(pr["sub_ms"], 1),
+                "merge_ms": round(pr["merge_ms"], 1), "final_ms": round(pr["final_ms"], 1),
+                "netsim": pr["final"]["netsim"], "n_exemplars": pr["final"]["n_exemplars"]},
+        "time_ratio_plain_over_pap": round(t_plain / t_pap, 3),
+        "netsim_rel_diff": (pr["final"]["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
+    }
+    del S, R, A
+    torch.cuda.empty_cache()
+
+    # ---- landmark AP: 1e6 points, 1000 Gaussians in R^128, 20000 uniform landmarks;
+    # plain AP is compared on the first 100000 points (1e6 points would need 12 TB)
+    X, _ = synth.workload(3)
+    Xd = torch.from_numpy(X).to(dev)
+    (idx, lm, lr), t_lap_full = timed(lambda: capi.lap_run(Xd, 20000, "uniform", seed=synth.config_seed(3),
+                                                           precision="bf16", damping=DAMPING,
+                                                           max_iter=MAX_ITER, conv_iter=CONV_ITER))
+    full = {"n": X.shape[0], "ms": round(t_lap_full, 1), "landmark_iters": lr["landmark"]["iters"],
+            "n_exemplars": lr["n_exemplars"], "netsim": lr["netsim"],
+            "assign_ms": round(lr["assign_ms"], 2), "landmark_ms": round(lr["landmark_ms"], 1)}
+    del Xd, idx, lm
+    m = 100000
+    Xs = torch.from_numpy(X[:m]).to(dev)
+    S, _ = capi.ap_similarity(Xs, precision="bf16")
+    R = capi.empty_square(m, dev, 0.0)
+    A = capi.empty_square(m, dev, 0.0)
+    (rp, exp_), t_plain = timed(plain)
+    del R, A
+    torch.cuda.empty_cache()
+    (_, _, ls), t_lap = timed(lambda: capi.lap_run(Xs, 20000, "uniform", seed=synth.config_seed(3),
+                                                   precision="bf16", damping=DAMPING,
+                                                   max_iter=MAX_ITER, conv_iter=CONV_ITER))
+    out["lap"] = {
+        "workload": "1000 Gaussians in R^128 (sigma 0.5, centres N(0,16I)); 20000 uniform landmarks",
+        "full_1e6": full,
+        "subsample": m,
+        "plain": {"iters": rp["iters"], "ms": round(t_plain, 1), "netsim": exp_["netsim"],
+                  "n_exemplars": exp_["n_exemplars"]},
+        "lap": {"landmark_iters": ls["landmark"]["iters"], "ms": round(t_lap, 1),
+                "netsim": ls["netsim"], "n_exemplars": ls["n_exemplars"]},
+        "time_ratio_plain_over_lap": round(t_plain / t_lap, 3),
+        "netsim_rel_diff": (ls["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
+    }
+    del S, Xs
+    torch.cuda.empty_cache()
+    return out
 
 
 def _oracle_sample(n_sample, seconds):
@@ -355,6 +449,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttc", action="store_true",
+                    help="skip the time-to-converge comparisons (partition and landmark AP)")
     ap.add_argument("--n", type=int, default=N_POINTS,
                     help="points (default: the 20000-point workload; smaller for profiling)")
     args = ap.parse_args()
