@@ -18,7 +18,7 @@ Two statements of one iteration are given:
   (equal to the maximum on a tie); the sum over i' not in {i,k} equals the
   column sum over i' != k minus the i-th term.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
   * R starts at zero, like A (Eq. 1 names only A).
   * "each message is set to lambda times its value from the previous
     iteration plus 1-lambda times its prescribed updated value" (Section 2):
