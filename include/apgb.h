@@ -149,7 +149,10 @@ int32_t   ap_preference_median(const float* S, int64_t n, int64_t ld, float* med
  *  out       host ap_result* (may be NULL): iters, converged (dpsim/expref/
  *            netsim are left 0; see ap_exemplars).  The call always
  *            synchronises ``stream`` before returning.
- *  Errors: AP_ERR_NONFINITE if S holds NaN/Inf (checked on the device first).
+ *  Errors: AP_ERR_NONFINITE if S holds NaN/Inf (checked on the device first);
+ *  AP_ERR_UNSUPPORTED if no sweep configuration fits n (a cluster of 16 CTAs
+ *  covers a row of at most 16 x 1920 float4, n <= 122880, which at 12 bytes
+ *  per element of S, R and A is about 180 GB).
  *  Returns AP_NOT_CONVERGED when conv_iter > 0 and max_iter was reached.
  * ------------------------------------------------------------------------- */
 size_t    ap_iterate_workspace_size(int64_t n, int64_t ld);

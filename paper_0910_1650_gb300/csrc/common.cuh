@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <math.h>
+#include <climits>
 
 #include "../../include/apgb.h"
 
@@ -130,6 +131,30 @@ __device__ __forceinline__ void argmax_warp(float& v, int& j) {
         int   j2 = __shfl_xor_sync(0xffffffffu, j, o);
         argmax_merge(v, j, v2, j2);
     }
+}
+
+// The same reductions with one redux.sync per quantity (sm_100 family):
+// m1 = warp max; j1 = lowest index among the lanes holding m1; m2 = max over
+// lanes of (their m1, or their m2 for the lane holding j1), since the lanes'
+// index sets are disjoint.  NaN inputs are ignored, as fmaxf does.
+__device__ __forceinline__ float warp_max_f32(float x) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ Top2 top2_warp_redux(Top2 t) {
+    Top2 r;
+    r.m1 = warp_max_f32(t.m1);
+    r.j1 = __reduce_min_sync(0xffffffffu, t.m1 == r.m1 ? t.j1 : INT_MAX);
+    r.m2 = warp_max_f32(t.j1 == r.j1 ? t.m2 : t.m1);
+    return r;
+}
+
+__device__ __forceinline__ void argmax_warp_redux(float& v, int& j) {
+    const float m = warp_max_f32(v);
+    j = __reduce_min_sync(0xffffffffu, v == m ? j : INT_MAX);
+    v = m;
 }
 
 }  // namespace apgb

@@ -81,6 +81,38 @@ def test_sweep_matches_oracle_fixed_iterations(name, lam, iters):
     assert np.array_equal(got, want)
 
 
+def test_every_sweep_configuration_matches_oracle():
+    """Every admissible launch configuration (cluster size x float4 per thread x
+    stages; two stages run rows unpipelined, three or more pipelined across the
+    cluster exchange) against the oracle, on a size with a ragged float4 tail."""
+    S = workload_S("ragged_5003")
+    n = S.shape[0]
+    Sd = dev_square(S)
+    ref = oap.run(S, lam=0.9, fixed_iters=4)
+    want_dec = None
+    tried = set()
+    try:
+        for C in (1, 2, 4, 8, 16):
+            for ept in (1, 2, 3, 4):
+                for ns in (2, 3, 4):
+                    try:
+                        capi.ap_sweep_set_config(n, C, ept, ns)
+                    except capi.ApgbError:
+                        continue
+                    cfg = capi.ap_sweep_get_config(n)
+                    R, A, res, dec = capi.ap_iterate(Sd, damping=0.9, max_iter=4, conv_iter=0)
+                    key = (cfg["cluster"], cfg["ept"], cfg["stages"], cfg["clusters"])
+                    tried.add(key)
+                    assert rel_inf(host(R), ref["R"]) <= TOL, key
+                    assert rel_inf(host(A), ref["A"]) <= TOL, key
+                    got = dec.cpu().numpy()
+                    assert np.array_equal(got, oap.decisions(host(R), host(A), dtype=np.float32)), key
+    finally:
+        capi.ap_sweep_set_config(n)
+    assert {k[2] for k in tried} >= {2, 3, 4}
+    assert {k[0] for k in tried} >= {1, 4, 16}
+
+
 def test_sweep_warm_start_and_padding():
     """Nonzero initial R/A (the Step 4 use of Algorithm 2) and an ld with
     padding columns that must stay untouched."""
