@@ -284,9 +284,47 @@ def run_gpu(args):
             del S, R, A, Xd
             torch.cuda.empty_cache()
             line["time_to_converge"] = time_to_converge(dev)
+            line["small_problem"] = small_problem(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def small_problem(dev, reps=20):
+    """The 500-point 2-D mixture (damping 0.5, max 200, 15 unchanged sweeps):
+    S, R and A (1 MB each) stay in L2, so a run is bound by launch latency,
+    not HBM.  Device time of whole ap_iterate calls (CUDA events) with the
+    iterations enqueued as CUDA graphs and as separate launches."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    X, _ = synth.workload(0)
+    S, _ = capi.ap_similarity(torch.from_numpy(X).to(dev), precision="fp32")
+    R = capi.empty_square(S.shape[0], dev, 0.0)
+    A = capi.empty_square(S.shape[0], dev, 0.0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"workload": "500 points in 2-D, 5 Gaussians (centres U[-10,10]^2, sigma 1); "
+                       "p = off-diagonal median; damping 0.5, max 200, 15 unchanged sweeps; "
+                       "L2-resident (roofline n/a)", "n": int(S.shape[0])}
+    for graph in (True, False):
+        def run():
+            R.zero_()
+            A.zero_()
+            return capi.ap_iterate(S, R, A, damping=0.5, max_iter=200, conv_iter=15,
+                                   graph=graph)[2]
+        r = run()                       # capture (graph) / warm-up
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            r = run()
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        key = "graph" if graph else "stream"
+        out[key] = {"iters": r["iters"], "ms_to_converge": round(ms, 4),
+                    "us_per_iter": round(ms * 1e3 / max(r["iters"], 1), 3)}
+    return out
 
 
 def time_to_converge(dev):

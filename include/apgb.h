@@ -71,8 +71,15 @@ typedef struct ap_params {
 } ap_params;
 
 /* ap_params.flags: bracket every sweep launch with CUDA events on the
- * caller's stream and report their summed duration in ap_result.sweep_ms. */
+ * caller's stream and report their summed duration in ap_result.sweep_ms
+ * (the iterations are then enqueued as separate launches). */
 #define AP_FLAG_TIME_SWEEP 1
+/* ap_params.flags: enqueue iterations as separate kernel launches.  By default
+ * each chunk of check_every iterations (m sweep + m column-sum launches) is
+ * one CUDA graph: captured on a library-owned stream the first time a
+ * workspace address and launch shape are seen, kept (up to 32 per process),
+ * and launched on the caller's stream. */
+#define AP_FLAG_NO_GRAPH   2
 
 /* Outputs of Algorithm 1 (Section 2): dpsim = sum of the data-point
  * similarities to their exemplars, expref = sum of the exemplars'

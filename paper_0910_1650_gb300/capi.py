@@ -23,6 +23,7 @@ AP_NO_EXEMPLARS = 2
 AP_PREC_FP32, AP_PREC_BF16 = 0, 1
 AP_PREF_MEDIAN, AP_PREF_SCALAR, AP_PREF_VECTOR = 0, 1, 2
 AP_FLAG_TIME_SWEEP = 1
+AP_FLAG_NO_GRAPH = 2
 AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
 AP_NOALLOC_MAX_N = 65536
@@ -257,9 +258,10 @@ def ap_preference_median(S, stream=None):
 
 
 def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check_every=0,
-               time_sweep=False, decisions=True, stream=None):
-    """Runs Algorithm 1 in place on (R, A) (zeros when omitted).
-    Returns (R, A, result dict, decisions int32 tensor or None)."""
+               time_sweep=False, decisions=True, graph=True, stream=None):
+    """Runs Algorithm 1 in place on (R, A) (zeros when omitted).  ``graph``:
+    enqueue each chunk of iterations as one CUDA graph (ignored with
+    ``time_sweep``).  Returns (R, A, result dict, decisions int32 tensor or None)."""
     _dev_f32(S, "S")
     n = S.shape[0]
     if R is None:
@@ -272,7 +274,7 @@ def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check
         raise ValueError("S, R and A must share one leading dimension")
     dec = torch.empty(n, dtype=torch.int32, device=S.device) if decisions else None
     p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every),
-                 AP_FLAG_TIME_SWEEP if time_sweep else 0)
+                 (AP_FLAG_TIME_SWEEP if time_sweep else 0) | (0 if graph else AP_FLAG_NO_GRAPH))
     res = ApResult()
     ws = workspace(lib().ap_iterate_workspace_size(n, S.stride(0)), S.device)
     st = lib().ap_iterate(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),

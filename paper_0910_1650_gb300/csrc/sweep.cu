@@ -32,6 +32,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -512,15 +513,29 @@ sweep_kernel(SweepLaunch L) {
 
 // Column sums in a fixed cluster order, then the stop rule (block 0 of each
 // problem).  Grid: (column blocks, problems).
-__global__ void finalize_kernel(const SweepArgs* __restrict__ table) {
+// Block: 32 columns x 8 lanes over the cluster partials; each lane sums every
+// 8th partial, then the 8 lane sums are added in a fixed tree, so the result
+// does not depend on the schedule.  Grid: (ceil(n/32), problems).
+constexpr int kFinCols = 32, kFinLanes = 8;
+
+__global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const SweepArgs* __restrict__ table) {
     const SweepArgs& a = table[blockIdx.y];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cx = threadIdx.x % kFinCols, gy = threadIdx.x / kFinCols;
+    const int k = blockIdx.x * kFinCols + cx;
     SweepState* st = a.st;
+    __shared__ float part[kFinLanes][kFinCols];
+    float s = 0.f;
     if (k < a.n) {
-        float s = 0.f;
-        for (int g = 0; g < a.G; ++g) s += a.pcol[(int64_t)g * a.n + k];
-        const_cast<float*>(a.colp)[k] = s;
-        const_cast<float*>(a.cvec)[k] = a.rkk[k] + s;
+#pragma unroll 4
+        for (int g = gy; g < a.G; g += kFinLanes) s += a.pcol[(int64_t)g * a.n + k];
+    }
+    part[gy][cx] = s;
+    __syncthreads();
+    if (gy == 0 && k < a.n) {
+        const float t = ((part[0][cx] + part[1][cx]) + (part[2][cx] + part[3][cx])) +
+                        ((part[4][cx] + part[5][cx]) + (part[6][cx] + part[7][cx]));
+        const_cast<float*>(a.colp)[k] = t;
+        const_cast<float*>(a.cvec)[k] = a.rkk[k] + t;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (st->done) return;
@@ -810,9 +825,11 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
     return cv.used;
 }
 
-static int32_t launch_sweep(const SweepConfig& c, int clusters, const SweepLaunch& L, cudaStream_t s) {
-    AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)c.smem));
+static int32_t launch_sweep(const SweepConfig& c, int clusters, const SweepLaunch& L, cudaStream_t s,
+                            bool set_attr = true) {
+    if (set_attr)
+        AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)c.smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.C * clusters, 1, 1);
     cfg.blockDim = dim3(c.T + 32, 1, 1);       // compute warps + the producer warp
@@ -844,6 +861,82 @@ static bool valid_params(const ap_params* p) {
     return p && p->damping >= 0.f && p->damping < 1.f && p->max_iter >= 1 && p->conv_iter >= 0;
 }
 
+// CUDA graphs of a chunk of iterations (m x {sweep, finalize}).  A chunk is
+// captured once on a library-owned stream of the current device and the
+// executable graph is kept, keyed by everything its launches bake in (the
+// problem table's address and the launch shape), so repeated calls with the
+// same workspace replay it.  All iteration state lives on the device, so a
+// replay continues where the previous one stopped.
+struct GraphKey {
+    int dev;
+    const void* table;
+    int count, C, EPT, NS, T, G, clusters, nmax;
+    size_t smem;
+    int64_t m;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(dev, table, count, C, EPT, NS, T, G, clusters, nmax, smem, m) <
+               std::tie(o.dev, o.table, o.count, o.C, o.EPT, o.NS, o.T, o.G, o.clusters, o.nmax,
+                        o.smem, o.m);
+    }
+};
+
+static std::mutex g_graph_mu;
+static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+static std::map<int, cudaStream_t> g_capture_stream;
+constexpr size_t kMaxGraphs = 32;
+
+static int32_t enqueue_chunk(const SweepConfig& c, const Plan& plan, const SweepLaunch& L,
+                             int64_t m, dim3 fin_grid, cudaStream_t s) {
+    for (int64_t j = 0; j < m; ++j) {
+        AP_TRY(launch_sweep(c, plan.clusters, L, s, false));
+        finalize_kernel<<<fin_grid, kFinCols * kFinLanes, 0, s>>>(L.table);
+    }
+    return last_error();
+}
+
+static int32_t launch_chunk_graph(const SweepConfig& c, const Plan& plan, const SweepLaunch& L,
+                                  int64_t m, dim3 fin_grid, cudaStream_t s) {
+    int dev = 0;
+    AP_CUDA_TRY(cudaGetDevice(&dev));
+    const GraphKey key{dev, L.table, L.count, c.C, c.EPT, c.NS, c.T, c.G, plan.clusters,
+                       plan.nmax, c.smem, m};
+    // the shared-memory ceiling is a function attribute, set outside the capture
+    AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)c.smem));
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        cudaStream_t cs;
+        auto sit = g_capture_stream.find(dev);
+        if (sit == g_capture_stream.end()) {
+            AP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            g_capture_stream[dev] = cs;
+        } else {
+            cs = sit->second;
+        }
+        AP_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const int32_t st = enqueue_chunk(c, plan, L, m, fin_grid, cs);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (st != AP_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return st != AP_OK ? st : AP_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return AP_ERR_CUDA;
+        if (g_graphs.size() >= kMaxGraphs) {
+            cudaGraphExecDestroy(g_graphs.begin()->second);
+            g_graphs.erase(g_graphs.begin());
+        }
+        it = g_graphs.emplace(key, exec).first;
+    }
+    AP_CUDA_TRY(cudaGraphLaunch(it->second, s));
+    return AP_OK;
+}
+
 // Runs Algorithm 1 on every problem of the batch until each has stopped.
 // out[b] receives problem b's result; sweep timing is per launch (shared).
 static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_result* out,
@@ -857,6 +950,7 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
                                 cudaMemcpyHostToDevice, s));
     const int nmax = plan.nmax;
     const dim3 col_grid((nmax + 255) / 256, count);
+    const dim3 fin_grid((nmax + kFinCols - 1) / kFinCols, count);
     sweep_init_kernel<<<col_grid, 256, 0, s>>>(w.table, p->max_iter, p->conv_iter);
     nonfinite_kernel<<<dim3(std::min(nmax, 1024), count), 256, 0, s>>>(w.table);
     note_launches(2);
@@ -891,13 +985,18 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     double sweep_ms = 0.0;
     int32_t t_before = 1;
     bool all_done = false;
+    const bool graph = !timed && !(p->flags & AP_FLAG_NO_GRAPH);
     while (launched < total) {
         const int64_t m = std::min<int64_t>(chunk, total - launched);
-        for (int64_t j = 0; j < m; ++j) {
-            if (timed) AP_CUDA_TRY(cudaEventRecord(ev.start[j], s));
-            AP_TRY(launch_sweep(c, plan.clusters, L, s));
-            if (timed) AP_CUDA_TRY(cudaEventRecord(ev.stop[j], s));
-            finalize_kernel<<<col_grid, 256, 0, s>>>(w.table);
+        if (graph) {
+            AP_TRY(launch_chunk_graph(c, plan, L, m, fin_grid, s));
+        } else {
+            for (int64_t j = 0; j < m; ++j) {
+                if (timed) AP_CUDA_TRY(cudaEventRecord(ev.start[j], s));
+                AP_TRY(launch_sweep(c, plan.clusters, L, s));
+                if (timed) AP_CUDA_TRY(cudaEventRecord(ev.stop[j], s));
+                finalize_kernel<<<fin_grid, kFinCols * kFinLanes, 0, s>>>(w.table);
+            }
         }
         note_launches(2 * (uint64_t)m);
         AP_TRY(last_error());

@@ -113,6 +113,25 @@ def test_every_sweep_configuration_matches_oracle():
     assert {k[0] for k in tried} >= {1, 4, 16}
 
 
+@pytest.mark.parametrize("name,lam,maxit,check", [("mix2d_500", 0.5, 200, 0), ("mix2d_500", 0.5, 200, 7),
+                                                   ("mix64_2000", 0.9, 300, 0)])
+def test_graph_launch_equals_stream_launch(name, lam, maxit, check):
+    """Chunks of iterations enqueued as CUDA graphs (the default) give the same
+    bits as separate launches, on the first call (capture) and on a repeat
+    call (cached graph), with a chunk size that does not divide the run."""
+    S = workload_S(name)
+    Sd = dev_square(S)
+    outs = []
+    for graph in (False, True, True):
+        R, A, res, dec = capi.ap_iterate(Sd, damping=lam, max_iter=maxit, conv_iter=15,
+                                         check_every=check, graph=graph)
+        outs.append((host(R), host(A), res["iters"], res["converged"], dec.cpu().numpy()))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+        assert o[2:4] == outs[0][2:4]
+        assert np.array_equal(o[4], outs[0][4])
+
+
 def test_sweep_warm_start_and_padding():
     """Nonzero initial R/A (the Step 4 use of Algorithm 2) and an ld with
     padding columns that must stay untouched."""
