@@ -285,6 +285,7 @@ def run_gpu(args):
             torch.cuda.empty_cache()
             line["time_to_converge"] = time_to_converge(dev)
             line["small_problem"] = small_problem(dev)
+            line["batch_learned"] = batch_learned(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -325,6 +326,58 @@ def small_problem(dev, reps=20):
         out[key] = {"iters": r["iters"], "ms_to_converge": round(ms, 4),
                     "us_per_iter": round(ms * 1e3 / max(r["iters"], 1), 3)}
     return out
+
+
+def batch_learned(dev, count=256, n_train=32):
+    """The batch workload: 256 independent problems of image-like vectors
+    (N uniform in [200, 4000], d = 4096).  S of every problem by the batched
+    tensor-core similarity; Algorithm 1 on all problems at once (one batched
+    sweep per iteration) from a cold start, and from the learned warm start
+    (network trained here on 32 further problems of the same generator),
+    each warm result judged against the cold one (net similarity within
+    0.5 %, else the cold result is kept).  Device times by CUDA events."""
+    import torch
+
+    from paper_0910_1650_gb300 import batched, learned, synth
+
+    sizes, _ = synth.batch_problem_sizes(count)
+    B = batched.Batch(batched.image_batch(count), sizes[:count])
+    peaks, src = _peaks()
+    tflops = B.gemm_flops / (B.sim_ms / 1e3) / 1e12
+    Rc, Ac, rc, ms_c = batched.run(B)
+    cold = batched.netsims(B, Rc, Ac)
+    del Rc, Ac
+    torch.cuda.empty_cache()
+    F, T, _ = learned.make_dataset(list(batched.image_batch(n_train, offset=count)))
+    P, P16, losses = learned.train(F, T, epochs=60, batch=4096, lr=2e-3)
+    Rw, Aw, ms_ws = batched.warm_start(B, P, P16)
+    Rw, Aw, rw, ms_w = batched.run(B, Rw, Aw)
+    warm = batched.netsims(B, Rw, Aw)
+    keep = batched.judge(cold, warm)
+    del Rw, Aw
+    torch.cuda.empty_cache()
+    it_c = [r["iters"] for r in rc]
+    it_w = [r["iters"] for r in rw]
+    rel = [abs(w[0] - c[0]) / abs(c[0]) for c, w in zip(cold, warm)]
+    return {
+        "workload": "256 problems, N ~ U{200..4000}, d = 4096 image-like vectors (rank-20 "
+                    "nonnegative templates, 5-40 clusters, + U[0,0.05] noise); damping 0.9, "
+                    "max 1000, 15 unchanged sweeps",
+        "sum_n2": float(sum(float(m) * m for m in B.n)),
+        "similarity": {"ms": round(B.sim_ms, 2), "tflops": round(tflops, 1),
+                       "frac_of_bf16_peak": round(tflops / peaks["bf16_tflops"], 4),
+                       "peak_source": src,
+                       "note": "whole batched similarity (means, centring, Gram product, "
+                               "median) over 2 n^2 d flops"},
+        "cold": {"ms": round(ms_c, 1), "iters_mean": round(sum(it_c) / count, 1),
+                 "iters_max": max(it_c), "converged": sum(r["converged"] for r in rc)},
+        "train": {"problems": n_train, "rows": int(F.shape[0]), "epochs": 60,
+                  "loss_first": round(losses[0], 4), "loss_last": round(losses[-1], 4)},
+        "warm": {"ms_warm_start": round(ms_ws, 1), "ms": round(ms_w, 1),
+                 "iters_mean": round(sum(it_w) / count, 1), "iters_max": max(it_w),
+                 "judge_keeps": sum(keep), "netsim_rel_diff_median": round(sorted(rel)[count // 2], 5)},
+        "time_ratio_cold_over_warm": round(ms_c / (ms_ws + ms_w), 3),
+    }
 
 
 def time_to_converge(dev):
@@ -477,6 +530,32 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def similarity_only(args):
+    """The similarity build alone (bf16 tensor-core Gram product with the
+    distance epilogue, plus means, centring and the median) on one image-like
+    problem: the tensor-bound case of the batch workload, for profiling."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    X, _ = synth.image_like(args.n, args.similarity_only, 20, stream=7)
+    Xd = torch.from_numpy(X).cuda()
+    S = capi.empty_square(args.n, "cuda")
+    for _ in range(args.warmup):
+        capi.ap_similarity(Xd, S=S, precision="bf16")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(args.steps):
+        capi.ap_similarity(Xd, S=S, precision="bf16")
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    fl = 2.0 * args.n * args.n * args.similarity_only
+    print(json.dumps({"case": "similarity", "n": args.n, "d": args.similarity_only,
+                      "ms": round(ms, 4), "tflops": round(fl / ms / 1e9, 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -491,7 +570,13 @@ def main():
                     help="skip the time-to-converge comparisons (partition and landmark AP)")
     ap.add_argument("--n", type=int, default=N_POINTS,
                     help="points (default: the 20000-point workload; smaller for profiling)")
+    ap.add_argument("--similarity-only", type=int, default=0, metavar="D",
+                    help="profiling aid: time the bf16 similarity build alone on one image-like "
+                         "problem of --n points and D features, print one JSON line")
     args = ap.parse_args()
+    if args.similarity_only:
+        similarity_only(args)
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

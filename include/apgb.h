@@ -126,6 +126,33 @@ int32_t   ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx,
                         void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * ap_similarity_batched -- ap_similarity for `count` independent problems
+ * with the same feature dimension d, in one call (no counterpart in the
+ * paper: a batch of independent Algorithm 1 inputs).
+ *
+ *  X        device float32; problem b's features are rows X + xoff[b]
+ *           (n[b] x d, leading dimension ldx).  xoff, n: host int64[count].
+ *  S        device float32; problem b's S at S + soff[b], n[b] x n[b] with
+ *           leading dimension lds[b] (soff, lds: host int64[count]).
+ *  precision, pref_mode as for ap_similarity (AP_PREF_MEDIAN: each
+ *           problem's own off-diagonal median; AP_PREF_SCALAR: host pref[0]
+ *           for every problem; AP_PREF_VECTOR is not accepted).  No noise.
+ *  pref_out host float[count] (may be NULL): the preference of each problem.
+ *  One workspace, sized for the largest problem, serves every problem in
+ *  turn: the problems' kernels are enqueued back to back on ``stream`` and
+ *  the stream is synchronised once, at the end.  Results equal ap_similarity
+ *  on each problem bit for bit.
+ *  Errors: AP_ERR_INVALID_ARG for a bad size or offset; AP_ERR_TIMEOUT as for
+ *  ap_similarity.
+ * ------------------------------------------------------------------------- */
+size_t    ap_similarity_batched_workspace_size(const int64_t* n, int32_t count, int64_t d);
+int32_t   ap_similarity_batched(const float* X, const int64_t* xoff, const int64_t* n,
+                                int32_t count, int64_t d, int64_t ldx, float* S,
+                                const int64_t* soff, const int64_t* lds, int32_t precision,
+                                int32_t pref_mode, const float* pref, float* pref_out,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * ap_preference_median -- the preference used when the paper's experiments
  * "adjust the input preference" to a common value (Section 5): the exact
  * median of the n(n-1) off-diagonal entries of S (the diagonal is ignored;

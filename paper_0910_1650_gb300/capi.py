@@ -104,6 +104,9 @@ _SIGNATURES = {
     "ap_similarity_workspace_size": (_SZ, [_I64, _I64]),
     "ap_similarity": (C.c_int32, [_P, _I64, _I64, _I64, _P, _I64, C.c_int32, C.c_int32, _P,
                                   C.c_double, C.c_uint64, _P, _P, _SZ, _P]),
+    "ap_similarity_batched_workspace_size": (_SZ, [_P, C.c_int32, _I64]),
+    "ap_similarity_batched": (C.c_int32, [_P, _P, _P, C.c_int32, _I64, _I64, _P, _P, _P,
+                                          C.c_int32, C.c_int32, _P, _P, _P, _SZ, _P]),
     "ap_preference_median_workspace_size": (_SZ, [_I64]),
     "ap_preference_median": (C.c_int32, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "ap_iterate_workspace_size": (_SZ, [_I64, _I64]),
@@ -242,6 +245,36 @@ def ap_similarity(X, S=None, precision="fp32", pref="median", noise_rel=0.0, see
                              ws.numel(), _stream(stream))
     _check("ap_similarity", st, ok=(AP_OK,))
     return S, float(out.value)
+
+
+def ap_similarity_batched(X, xoff, n, S, soff, lds, precision="bf16", pref="median",
+                          stream=None):
+    """ap_similarity for several problems in one call.  X: float32 CUDA
+    tensor (rows of every problem, same d; 2-D), problem b's rows start at
+    element offset xoff[b]; S: 1-D float32 CUDA arena, problem b's n[b] x n[b]
+    matrix at element offset soff[b] with leading dimension lds[b].
+    Returns the list of preferences."""
+    _dev_f32(X, "X")
+    if not (S.is_cuda and S.dtype == torch.float32 and S.is_contiguous()):
+        raise TypeError("S must be a contiguous float32 CUDA tensor")
+    d, ldx = X.shape[1], X.stride(0)
+    count = len(n)
+    prec = {"fp32": AP_PREC_FP32, "bf16": AP_PREC_BF16}[precision]
+    if isinstance(pref, str):
+        mode, pptr, keep = AP_PREF_MEDIAN, None, None
+    else:
+        keep = (C.c_float * 1)(float(pref))
+        mode, pptr = AP_PREF_SCALAR, C.cast(keep, C.c_void_p)
+    xo, na, so, la = _i64_array(xoff), _i64_array(n), _i64_array(soff), _i64_array(lds)
+    out = (C.c_float * count)()
+    ws = workspace(lib().ap_similarity_batched_workspace_size(C.cast(na, C.c_void_p), count, d),
+                   X.device)
+    st = lib().ap_similarity_batched(_ptr(X), C.cast(xo, C.c_void_p), C.cast(na, C.c_void_p), count,
+                                     d, ldx, _ptr(S), C.cast(so, C.c_void_p), C.cast(la, C.c_void_p),
+                                     prec, mode, pptr, C.cast(out, C.c_void_p), _ptr(ws), ws.numel(),
+                                     _stream(stream))
+    _check("ap_similarity_batched", st, ok=(AP_OK,))
+    return [float(v) for v in out]
 
 
 def ap_preference_median(S, stream=None):

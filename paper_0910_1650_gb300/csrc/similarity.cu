@@ -18,6 +18,8 @@
 
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace apgb {
@@ -27,15 +29,36 @@ int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int
 size_t tc_similarity_pad_rows();
 
 // ---- 1. column means -----------------------------------------------------------
-__global__ void colsum_partial_kernel(const float* __restrict__ X, int n, int d, int64_t ldx,
-                                      int rows_per_block, double* part) {
-    const int r0 = blockIdx.x * rows_per_block;
-    const int r1 = min(n, r0 + rows_per_block);
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        for (int i = r0; i < r1; ++i) s += (double)X[(int64_t)i * ldx + j];
-        part[(int64_t)blockIdx.x * d + j] = s;
+// Column sums of X in float64 over blocks of kMeanRows rows.  Block: 32
+// columns x 8 row lanes; lane y sums rows y, y+8, ... of the row block, and
+// the 8 lane sums are added in a fixed tree (deterministic).  Grid:
+// (ceil(d/32), ceil(n/kMeanRows)).  part[row block][j].
+constexpr int kMeanRows = 256;
+
+__global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ X, int n, int d,
+                                                             int64_t ldx, double* part) {
+    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + cx;
+    const int r0 = blockIdx.y * kMeanRows;
+    const int r1 = min(n, r0 + kMeanRows);
+    __shared__ double ps[8][32];
+    // Neumaier-compensated float32 sum of the lane's rows (float64 arithmetic is
+    // scarce on this part); (s, c) carries the sum to well below float32 rounding
+    float sm = 0.f, cm = 0.f;
+    if (j < d) {
+#pragma unroll 8
+        for (int i = r0 + ry; i < r1; i += 8) {
+            const float x = X[(int64_t)i * ldx + j];
+            const float t = sm + x;
+            cm += (fabsf(sm) >= fabsf(x)) ? (sm - t) + x : (x - t) + sm;
+            sm = t;
+        }
     }
+    ps[ry][cx] = (double)sm + (double)cm;
+    __syncthreads();
+    if (ry == 0 && j < d)
+        part[(int64_t)blockIdx.y * d + j] = ((ps[0][cx] + ps[1][cx]) + (ps[2][cx] + ps[3][cx])) +
+                                            ((ps[4][cx] + ps[5][cx]) + (ps[6][cx] + ps[7][cx]));
 }
 
 __global__ void colmean_kernel(const double* __restrict__ part, int nb, int d, int n,
@@ -160,50 +183,109 @@ struct SelectState {
 
 // Pass: histogram of the digit at `shift` among entries whose known high bits
 // match each target's prefix.
-__global__ void radix_hist_kernel(const float* __restrict__ S, int n, int64_t lds, int shift,
-                                  int bits, const SelectState* __restrict__ st,
-                                  unsigned long long* hist) {
+// Histogram of digit (key >> shift) & (2^bits - 1) over the off-diagonal keys
+// that match each order statistic's known prefix.  While both statistics
+// share their prefix (always in the first pass, usually later), one histogram
+// serves both.  VEC: rows read as float4 (S 16-byte aligned, lds % 4 == 0).
+template <bool VEC>
+__global__ void __launch_bounds__(256) radix_hist_kernel(const float* __restrict__ S, int n,
+                                                         int64_t lds, int shift, int bits,
+                                                         const SelectState* __restrict__ st,
+                                                         unsigned long long* hist) {
     __shared__ unsigned int h[2][2048];
     const int nb = 1 << bits;
     for (int b = threadIdx.x; b < 2 * 2048; b += blockDim.x) (&h[0][0])[b] = 0;
     __syncthreads();
     const uint32_t km = st->known_mask, p0 = st->prefix[0], p1 = st->prefix[1];
+    const bool same = p0 == p1;
     const uint32_t dm = (uint32_t)nb - 1u;
+    auto count = [&](float v) {
+        const uint32_t key = float_key(v);
+        const uint32_t dg = (key >> shift) & dm;
+        if ((key & km) == p0) atomicAdd(&h[0][dg], 1u);
+        if (!same && (key & km) == p1) atomicAdd(&h[1][dg], 1u);
+    };
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const float* row = S + (int64_t)i * lds;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            if (k == i) continue;
-            const uint32_t key = float_key(row[k]);
-            const uint32_t dg = (key >> shift) & dm;
-            if ((key & km) == p0) atomicAdd(&h[0][dg], 1u);
-            if ((key & km) == p1) atomicAdd(&h[1][dg], 1u);
+        if (VEC) {
+            const float4* row4 = reinterpret_cast<const float4*>(row);
+            const int n4 = (n + 3) >> 2;
+            for (int k4 = threadIdx.x; k4 < n4; k4 += blockDim.x) {
+                const float4 v = row4[k4];
+                const int k = 4 * k4;
+                if (k != i && k < n) count(v.x);
+                if (k + 1 != i && k + 1 < n) count(v.y);
+                if (k + 2 != i && k + 2 < n) count(v.z);
+                if (k + 3 != i && k + 3 < n) count(v.w);
+            }
+        } else {
+            for (int k = threadIdx.x; k < n; k += blockDim.x)
+                if (k != i) count(row[k]);
         }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        if (h[0][b]) atomicAdd(&hist[b], (unsigned long long)h[0][b]);
-        if (h[1][b]) atomicAdd(&hist[2048 + b], (unsigned long long)h[1][b]);
+        const unsigned int c0 = h[0][b], c1 = same ? c0 : h[1][b];
+        if (c0) atomicAdd(&hist[b], (unsigned long long)c0);
+        if (c1) atomicAdd(&hist[2048 + b], (unsigned long long)c1);
     }
 }
 
-__global__ void radix_scan_kernel(SelectState* st, unsigned long long* hist, int shift, int bits) {
-    if (threadIdx.x >= 2) return;
-    const int j = threadIdx.x;
+// For each order statistic: the bin holding its remaining rank (a block-wide
+// exclusive scan of the counts; each of the 1024 threads owns 2 bins), then
+// the prefix, rank and known-digit mask are advanced and the histograms
+// cleared for the next pass.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(SelectState* st, unsigned long long* hist,
+                                                          int shift, int bits) {
     const int nb = 1 << bits;
-    unsigned long long* h = hist + 2048 * j;
-    uint64_t r = st->rank[j];
-    int b = 0;
-    for (; b < nb; ++b) {
-        if (r < h[b]) break;
-        r -= h[b];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __shared__ unsigned long long wsum[32];
+    __shared__ int found[2];
+    __shared__ unsigned long long rem[2];
+    if (t < 2) {
+        found[t] = nb - 1;          // kept only if the counts were inconsistent
+        rem[t] = st->rank[t];
     }
-    if (b >= nb) b = nb - 1;     // unreachable when the counts are consistent
-    st->prefix[j] |= (uint32_t)b << shift;
-    st->rank[j] = r;
-    __syncwarp(0x3u);
-    for (int x = j; x < nb; x += 2) { hist[x] = 0; hist[2048 + x] = 0; }
-    __syncwarp(0x3u);
-    if (j == 0) st->known_mask |= (uint32_t)(nb - 1) << shift;
+    __syncthreads();
+    for (int j = 0; j < 2; ++j) {
+        const unsigned long long* h = hist + 2048 * j;
+        const unsigned long long r = st->rank[j];
+        const int b0 = 2 * t;
+        const unsigned long long c0 = b0 < nb ? h[b0] : 0ull, c1 = b0 + 1 < nb ? h[b0 + 1] : 0ull;
+        unsigned long long x = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long v = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const unsigned long long base = (warp > 0 ? wsum[warp - 1] : 0ull) + x - (c0 + c1);
+        if (r >= base && r < base + c0) {
+            found[j] = b0;
+            rem[j] = r - base;
+        } else if (r >= base + c0 && r < base + c0 + c1) {
+            found[j] = b0 + 1;
+            rem[j] = r - base - c0;
+        }
+        __syncthreads();
+    }
+    if (t < 2) {
+        st->prefix[t] |= (uint32_t)found[t] << shift;
+        st->rank[t] = rem[t];
+    }
+    if (t == 0) st->known_mask |= (uint32_t)(nb - 1) << shift;
+    for (int b = t; b < 2 * 2048; b += blockDim.x) hist[b] = 0;
 }
 
 __global__ void select_init_kernel(SelectState* st, unsigned long long* hist, uint64_t r0,
@@ -259,7 +341,7 @@ static int pad_rows(int n) {
     return (n + t - 1) / t * t;
 }
 static int pad_dim(int d) { return (d + 63) / 64 * 64; }
-static int mean_blocks(int n) { return (n + 1023) / 1024; }
+static int mean_blocks(int n) { return (n + kMeanRows - 1) / kMeanRows; }
 
 static size_t carve_sim(void* ws, int64_t n, int64_t d, SimWs* w) {
     Carver c(ws);
@@ -282,8 +364,11 @@ int32_t median_offdiag(const float* S, int n, int64_t lds, SelectState* sel,
     const int grid = std::min(n, 4096);
     const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
     for (int p = 0; p < 3; ++p) {
-        radix_hist_kernel<<<grid, 256, 0, s>>>(S, n, lds, shifts[p], bits[p], sel, hist);
-        radix_scan_kernel<<<1, 32, 0, s>>>(sel, hist, shifts[p], bits[p]);
+        if (aligned16(S) && (lds & 3) == 0)
+            radix_hist_kernel<true><<<grid, 256, 0, s>>>(S, n, lds, shifts[p], bits[p], sel, hist);
+        else
+            radix_hist_kernel<false><<<grid, 256, 0, s>>>(S, n, lds, shifts[p], bits[p], sel, hist);
+        radix_scan_kernel<<<1, 1024, 0, s>>>(sel, hist, shifts[p], bits[p]);
     }
     select_finish_kernel<<<1, 1, 0, s>>>(sel, pref);
     note_launches(8);
@@ -300,27 +385,19 @@ APGB_API size_t ap_similarity_workspace_size(int64_t n, int64_t d) {
     return carve_sim(nullptr, n, d, &w);
 }
 
-APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx, float* S,
-                               int64_t lds, int32_t precision, int32_t pref_mode,
-                               const float* pref, double noise_rel, uint64_t seed,
-                               float* pref_out, void* ws, size_t ws_bytes, void* stream) {
-    if (!X || !S || n < 2 || d < 1 || ldx < d || lds < n || n > INT_MAX / 2 || d > 65536)
-        return AP_ERR_INVALID_ARG;
-    if (precision != AP_PREC_FP32 && precision != AP_PREC_BF16) return AP_ERR_INVALID_ARG;
-    if (pref_mode != AP_PREF_MEDIAN && pref_mode != AP_PREF_SCALAR && pref_mode != AP_PREF_VECTOR)
-        return AP_ERR_INVALID_ARG;
-    if (pref_mode != AP_PREF_MEDIAN && !pref) return AP_ERR_INVALID_ARG;
-    if (!(noise_rel >= 0.0) || !std::isfinite(noise_rel)) return AP_ERR_INVALID_ARG;
-    AP_TRY(require_sm103());
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    SimWs w;
-    AP_TRY(check_ws(ws, ws_bytes, carve_sim(nullptr, n, d, &w)));
-    carve_sim(ws, n, d, &w);
-    const int ni = (int)n, di = (int)d;
-    const int npad = pad_rows(ni), dpad = pad_dim(di);
+namespace apgb {
 
+// Enqueues the whole similarity build of one problem on s (no synchronisation):
+// means, centring (+ bf16 rounding), the Gram product with the distance
+// epilogue, the preference and the optional noise.  pref_dev receives the
+// median (AP_PREF_MEDIAN); err the tensor-core kernel's error flag.
+static int32_t similarity_enqueue(const float* X, int ni, int di, int64_t ldx, float* S, int64_t lds,
+                                  int32_t precision, int32_t pref_mode, const float* pref,
+                                  double noise_rel, uint64_t seed, const SimWs& w, float* pref_dev,
+                                  int32_t* err, cudaStream_t s) {
+    const int npad = pad_rows(ni), dpad = pad_dim(di);
     const int nb = mean_blocks(ni);
-    colsum_partial_kernel<<<nb, 256, 0, s>>>(X, ni, di, ldx, 1024, w.part);
+    colsum_partial_kernel<<<dim3((di + 31) / 32, nb), 256, 0, s>>>(X, ni, di, ldx, w.part);
     colmean_kernel<<<(di + 255) / 256, 256, 0, s>>>(w.part, nb, di, ni, w.mean);
     const int cgrid = std::min((npad + 7) / 8, 65535);
     if (precision == AP_PREC_FP32) {
@@ -333,18 +410,14 @@ APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx
     } else {
         centre_kernel<true><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
         AP_TRY(last_error());
-        AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
         AP_TRY(tc_similarity_bf16(static_cast<const __nv_bfloat16*>(w.xc), w.nrm, ni, dpad, S, lds,
-                                  w.err, s));
+                                  err, s));
     }
-
-    float used = NAN;
     if (pref_mode == AP_PREF_MEDIAN) {
-        AP_TRY(median_offdiag(S, ni, lds, w.sel, w.hist, w.pref, s));
-        diag_kernel<<<(ni + 255) / 256, 256, 0, s>>>(S, ni, lds, nullptr, w.pref, 0.f);
+        AP_TRY(median_offdiag(S, ni, lds, w.sel, w.hist, pref_dev, s));
+        diag_kernel<<<(ni + 255) / 256, 256, 0, s>>>(S, ni, lds, nullptr, pref_dev, 0.f);
     } else if (pref_mode == AP_PREF_SCALAR) {
-        used = pref[0];
-        diag_kernel<<<(ni + 255) / 256, 256, 0, s>>>(S, ni, lds, nullptr, nullptr, used);
+        diag_kernel<<<(ni + 255) / 256, 256, 0, s>>>(S, ni, lds, nullptr, nullptr, pref[0]);
     } else {
         diag_kernel<<<(ni + 255) / 256, 256, 0, s>>>(S, ni, lds, pref, nullptr, 0.f);
     }
@@ -352,17 +425,96 @@ APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx
         noise_kernel<<<std::min(ni, 8192), 256, 0, s>>>(S, ni, lds, noise_rel, seed);
         note_launches(1);
     }
-    note_launches(precision == AP_PREC_FP32 ? 5 : 3);   // means(2), centre, GEMM, diagonal
-    AP_TRY(last_error());
-    float v = used;
+    note_launches(precision == AP_PREC_FP32 ? 5 : 4);   // means(2), centre, GEMM, diagonal
+    return last_error();
+}
+
+static bool sim_args_ok(int32_t precision, int32_t pref_mode, const float* pref, double noise_rel) {
+    if (precision != AP_PREC_FP32 && precision != AP_PREC_BF16) return false;
+    if (pref_mode != AP_PREF_MEDIAN && pref_mode != AP_PREF_SCALAR && pref_mode != AP_PREF_VECTOR)
+        return false;
+    if (pref_mode != AP_PREF_MEDIAN && !pref) return false;
+    return noise_rel >= 0.0 && std::isfinite(noise_rel);
+}
+
+}  // namespace apgb
+
+APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx, float* S,
+                               int64_t lds, int32_t precision, int32_t pref_mode,
+                               const float* pref, double noise_rel, uint64_t seed,
+                               float* pref_out, void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !S || n < 2 || d < 1 || ldx < d || lds < n || n > INT_MAX / 2 || d > 65536)
+        return AP_ERR_INVALID_ARG;
+    if (!sim_args_ok(precision, pref_mode, pref, noise_rel)) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SimWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_sim(nullptr, n, d, &w)));
+    carve_sim(ws, n, d, &w);
+    AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+    AP_TRY(similarity_enqueue(X, (int)n, (int)d, ldx, S, lds, precision, pref_mode, pref, noise_rel,
+                              seed, w, w.pref, w.err, s));
+    float v = pref_mode == AP_PREF_SCALAR ? pref[0] : NAN;
     int32_t err = 0;
     if (pref_mode == AP_PREF_MEDIAN)
         AP_CUDA_TRY(cudaMemcpyAsync(&v, w.pref, sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (precision == AP_PREC_BF16)
-        AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AP_CUDA_TRY(cudaStreamSynchronize(s));
     if (err) return AP_ERR_TIMEOUT;
     if (pref_out) *pref_out = v;
+    return AP_OK;
+}
+
+APGB_API size_t ap_similarity_batched_workspace_size(const int64_t* n, int32_t count, int64_t d) {
+    if (!n || count < 1 || d < 1 || d > 65536) return 0;
+    int64_t nmax = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        if (n[b] < 2 || n[b] > INT_MAX / 2) return 0;
+        nmax = std::max(nmax, n[b]);
+    }
+    SimWs w;
+    Carver c(nullptr);
+    c.take<unsigned char>(carve_sim(nullptr, nmax, d, &w));
+    c.take<float>((size_t)count);
+    return c.used;
+}
+
+APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, const int64_t* n,
+                                       int32_t count, int64_t d, int64_t ldx, float* S,
+                                       const int64_t* soff, const int64_t* lds, int32_t precision,
+                                       int32_t pref_mode, const float* pref, float* pref_out,
+                                       void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !xoff || !n || !S || !soff || !lds || count < 1 || d < 1 || ldx < d || d > 65536)
+        return AP_ERR_INVALID_ARG;
+    if (pref_mode == AP_PREF_VECTOR || !sim_args_ok(precision, pref_mode, pref, 0.0))
+        return AP_ERR_INVALID_ARG;
+    int64_t nmax = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        if (n[b] < 2 || n[b] > INT_MAX / 2 || lds[b] < n[b] || xoff[b] < 0 || soff[b] < 0)
+            return AP_ERR_INVALID_ARG;
+        nmax = std::max(nmax, n[b]);
+    }
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    AP_TRY(check_ws(ws, ws_bytes, ap_similarity_batched_workspace_size(n, count, d)));
+    SimWs w;
+    Carver c(ws);
+    c.take<unsigned char>(carve_sim(nullptr, nmax, d, &w));
+    carve_sim(ws, nmax, d, &w);
+    float* prefs = c.take<float>((size_t)count);
+    AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+    for (int32_t b = 0; b < count; ++b)
+        AP_TRY(similarity_enqueue(X + xoff[b], (int)n[b], (int)d, ldx, S + soff[b], lds[b], precision,
+                                  pref_mode, pref, 0.0, 0, w, prefs + b, w.err, s));
+    std::vector<float> v(count, pref_mode == AP_PREF_SCALAR ? pref[0] : NAN);
+    int32_t err = 0;
+    if (pref_mode == AP_PREF_MEDIAN)
+        AP_CUDA_TRY(cudaMemcpyAsync(v.data(), prefs, sizeof(float) * count, cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return AP_ERR_TIMEOUT;
+    if (pref_out)
+        for (int32_t b = 0; b < count; ++b) pref_out[b] = v[b];
     return AP_OK;
 }
 

@@ -68,6 +68,13 @@ struct Params {
     int32_t* arg;                   // ARGMAX: best column per row
     float* best;                    // ARGMAX: best score per row (may be null)
     int diag_zero;                  // SIM: write 0 where row == column
+    // SIM: the tensor store covers columns [0, n4), n4 = N rounded down to a
+    // multiple of 4 (a TMA store writes whole 16-byte granules at the right
+    // edge of the tensor, which would reach into the caller's columns >= N);
+    // columns [n4, N) are written by plain stores to out (row stride lds).
+    int n4;
+    float* out;
+    int64_t lds;
     uint32_t spin_limit;
     int32_t* error;
 };
@@ -342,10 +349,25 @@ __global__ void __launch_bounds__(THREADS, 1)
                             *reinterpret_cast<float4*>(buf + row_in_tile * 128 + phys * 16) =
                                 make_float4(o[0], o[1], o[2], o[3]);
                         }
+                        const int c0 = n * BN + c * OUT_COLS;     // first column of the chunk
+                        if (c0 + OUT_COLS > p.n4 && c0 < p.N && i < p.M) {
+                            // the ragged columns [n4, N) of this row
+#pragma unroll
+                            for (int e = 0; e < OUT_COLS; ++e) {
+                                const int k = c0 + e;
+                                if (k >= p.n4 && k < p.N)
+                                    p.out[(int64_t)i * p.lds + k] =
+                                        (p.diag_zero && k == i)
+                                            ? 0.f
+                                            : fminf(0.f, 2.f * v[e] - ai - sm.bnrm[acc][c * OUT_COLS + e]);
+                            }
+                        }
                         ptx::fence_proxy_async_smem();
                         named_barrier(1, 128);
                         if (et == 0) {
-                            tma_store_2d(&tmOut, n * BN + c * OUT_COLS, m * BM, buf);
+                            if (c0 < p.n4) {
+                                tma_store_2d(&tmOut, c0, m * BM, buf);
+                            }
                             ptx::bulk_commit();
                         }
                         ob ^= 1;
@@ -444,7 +466,8 @@ int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int
                     BK, BM, CU_TENSOR_MAP_SWIZZLE_128B));
     AP_TRY(make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)Xb, dpad, npad, (uint64_t)dpad * 2,
                     BK, BN, CU_TENSOR_MAP_SWIZZLE_128B));
-    AP_TRY(make_map(&mo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, S, (uint64_t)n, (uint64_t)n,
+    const int n4 = n & ~3;
+    AP_TRY(make_map(&mo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, S, (uint64_t)std::max(n4, 4), (uint64_t)n,
                     (uint64_t)lds * 4, OUT_COLS, BM, CU_TENSOR_MAP_SWIZZLE_128B));
     Params p{};
     p.M = n;
@@ -454,6 +477,9 @@ int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int
     p.anrm = nrm;
     p.bnrm = nrm;
     p.diag_zero = 1;
+    p.n4 = n4;
+    p.out = S;
+    p.lds = lds;
     p.spin_limit = 1u << 22;
     p.error = err;
     const int units = ((n + BM - 1) / BM) * ((n + BN - 1) / BN);

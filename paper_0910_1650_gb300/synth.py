@@ -203,6 +203,13 @@ def image_like(n: int, d: int = 4096, n_clusters: int = 10, rank: int = 20,
     return np.clip(X, 0.0, 1.0).astype(np.float32), labels.astype(np.int32)
 
 
+def image_like_task(args):
+    """``image_like`` for a process pool: args = (n, d, n_clusters, seed,
+    stream); returns X only."""
+    n, d, k, seed, stream = args
+    return image_like(n, d, k, seed=seed, stream=stream)[0]
+
+
 def batch_problem_sizes(count: int = 256, lo: int = 200, hi: int = 4000,
                         seed: int = config_seed(4)):
     """Sizes N_b ~ U{lo..hi} and cluster counts ~ U{5..40} of a batch of
