@@ -338,23 +338,24 @@ def batch_learned(dev, count=256, n_train=32):
     0.5 %, else the cold result is kept).  Device times by CUDA events."""
     import torch
 
-    from paper_0910_1650_gb300 import batched, learned, synth
+    from paper_0910_1650_gb300 import batched, capi, learned, synth
 
     sizes, _ = synth.batch_problem_sizes(count)
     B = batched.Batch(batched.image_batch(count), sizes[:count])
     peaks, src = _peaks()
     tflops = B.gemm_flops / (B.sim_ms / 1e3) / 1e12
-    Rc, Ac, rc, ms_c = batched.run(B)
-    cold = batched.netsims(B, Rc, Ac)
-    del Rc, Ac
-    torch.cuda.empty_cache()
+    R = torch.zeros_like(B.S)
+    A = torch.zeros_like(B.S)
+    ws = capi.ap_iterate_batched_workspace(B.n, B.ld, B.S.device)
+    R, A, rc, ms_c = batched.run(B, R, A, ws=ws)
+    cold = batched.netsims(B, R, A)
     F, T, _ = learned.make_dataset(list(batched.image_batch(n_train, offset=count)))
     P, P16, losses = learned.train(F, T, epochs=60, batch=4096, lr=2e-3)
-    Rw, Aw, ms_ws = batched.warm_start(B, P, P16)
-    Rw, Aw, rw, ms_w = batched.run(B, Rw, Aw)
-    warm = batched.netsims(B, Rw, Aw)
+    R, A, ms_ws = batched.warm_start(B, P, P16, R=R, A=A)
+    R, A, rw, ms_w = batched.run(B, R, A, ws=ws)
+    warm = batched.netsims(B, R, A)
     keep = batched.judge(cold, warm)
-    del Rw, Aw
+    del R, A, ws
     torch.cuda.empty_cache()
     it_c = [r["iters"] for r in rc]
     it_w = [r["iters"] for r in rw]
@@ -385,12 +386,14 @@ def time_to_converge(dev):
     on the same inputs (device time, CUDA events), with net similarities."""
     import torch
 
-    from paper_0910_1650_gb300 import capi, synth
+    from paper_0910_1650_gb300 import capi, learned, synth
 
     out = {}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(fn):
+        fn()                        # untimed first run: allocator misses stay outside
+        torch.cuda.synchronize()
         ev[0].record()
         r = fn()
         ev[1].record()
@@ -442,7 +445,27 @@ def time_to_converge(dev):
     full = {"n": X.shape[0], "ms": round(t_lap_full, 1), "landmark_iters": lr["landmark"]["iters"],
             "n_exemplars": lr["n_exemplars"], "netsim": lr["netsim"],
             "assign_ms": round(lr["assign_ms"], 2), "landmark_ms": round(lr["landmark_ms"], 1)}
-    del Xd, idx, lm
+    del idx, lm
+    # landmarks by the learned exemplar score (network trained on mixtures of
+    # the landmark pool's density), against uniform landmarks
+    t0 = time.perf_counter()
+    Fl, Tl, _ = learned.make_dataset(learned.landmark_training_problems())
+    Pl, P16l, ll = learned.train(Fl, Tl, epochs=60, batch=4096, lr=2e-3)
+    train_s = time.perf_counter() - t0
+
+    def lap_learned(Xv):
+        score, t_sc = timed(lambda: learned.landmark_scores(Xv, 20000, Pl, P16l))
+        (_, _, r), t = timed(lambda: capi.lap_run(Xv, 20000, "score", score=score, precision="bf16",
+                                                  damping=DAMPING, max_iter=MAX_ITER,
+                                                  conv_iter=CONV_ITER))
+        return {"ms": round(t_sc + t, 1), "score_ms": round(t_sc, 1),
+                "landmark_iters": r["landmark"]["iters"], "n_exemplars": r["n_exemplars"],
+                "netsim": r["netsim"]}
+
+    full["learned_landmarks"] = lap_learned(Xd)
+    full["learned_landmarks"]["netsim_rel_vs_uniform"] = (
+        (full["learned_landmarks"]["netsim"] - full["netsim"]) / abs(full["netsim"]))
+    del Xd
     m = 100000
     Xs = torch.from_numpy(X[:m]).to(dev)
     S, _ = capi.ap_similarity(Xs, precision="bf16")
@@ -454,8 +477,14 @@ def time_to_converge(dev):
     (_, _, ls), t_lap = timed(lambda: capi.lap_run(Xs, 20000, "uniform", seed=synth.config_seed(3),
                                                    precision="bf16", damping=DAMPING,
                                                    max_iter=MAX_ITER, conv_iter=CONV_ITER))
+    lrn = lap_learned(Xs)
     out["lap"] = {
-        "workload": "1000 Gaussians in R^128 (sigma 0.5, centres N(0,16I)); 20000 uniform landmarks",
+        "workload": "1000 Gaussians in R^128 (sigma 0.5, centres N(0,16I)); 20000 uniform landmarks; "
+                    "learned: the 20000 best exemplar scores of a 40000-point uniform pool",
+        "scorer_training": {"problems": 12, "rows": int(Fl.shape[0]), "loss_first": round(ll[0], 4),
+                            "loss_last": round(ll[-1], 4), "wall_s": round(train_s, 1)},
+        "lap_learned": dict(lrn, time_ratio_plain_over_lap=round(t_plain / lrn["ms"], 3),
+                            netsim_rel_diff=(lrn["netsim"] - exp_["netsim"]) / abs(exp_["netsim"])),
         "full_1e6": full,
         "subsample": m,
         "plain": {"iters": rp["iters"], "ms": round(t_plain, 1), "netsim": exp_["netsim"],

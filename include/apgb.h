@@ -285,27 +285,38 @@ int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_l
  * and its exemplar score can choose Algorithm 3's landmarks (the non-uniform
  * landmark selection Section 4 leaves to future work).
  *
- * Features of point k (APL_IN = 19): the 16 largest off-diagonal s(k,j) in
- * decreasing order, the mean and standard deviation of the off-diagonal
- * s(k,j), and s(k,k), all divided by `scale` (> 0, e.g. |median preference|).
- * Network 19 -> 256 -> 256 -> 3 with ReLU; outputs (r_hat, a_hat, logit):
+ * Features of point k (APL_IN = 25), with `scale` > 0 (e.g. |median
+ * preference|):
+ *   0-15  the 16 largest off-diagonal s(k,j), decreasing (ties: lower j
+ *         first), divided by scale;
+ *   16-17 mean and standard deviation of the off-diagonal s(k,j), / scale;
+ *   18    s(k,k) / scale;
+ *   19-22 log(1 + #{j != k : s(k,j) >= -q*scale}), q = 1/8, 1/4, 1/2, 1
+ *         (thresholds formed in float32);
+ *   23    D(k) - max D(j) over the 16 neighbours j of features 0-15, where
+ *         D = feature 20;
+ *   24    the fraction of those neighbours with D(j) > D(k).
+ * Network 25 -> 256 -> 256 -> 3 with ReLU; outputs (r_hat, a_hat, logit):
  * predicted converged r(k,k)/scale, a(k,k)/scale and exemplar log-odds.
  * The input is first standardised, x -> (x - mu) * isd, with mu and isd
  * fixed (set by the caller from training features; their gradient is zero).
- * Parameters: one flat float32 vector of apl_param_count() entries (W1 256x19,
- * b1, W2 256x256, b2, W3 3x256, b3, mu 19, isd 19, row-major), plus a bf16
+ * Parameters: one flat float32 vector of apl_param_count() entries (W1 256x25,
+ * b1, W2 256x256, b2, W3 3x256, b3, mu 25, isd 25, row-major), plus a bf16
  * copy (same offsets) that the products use with fp32 accumulation.
  * Training loss (mean over rows): (r_hat - t_r)^2 + (a_hat - t_a)^2 +
  * softplus(logit) - t_e * logit; Adam (0.9, 0.999, 1e-8, bias-corrected).
  * All device pointers are caller-owned; rows-sized scratch comes from `ws`
  * (apl_workspace_size(rows) bytes).  The calls below enqueue work only.
  * ------------------------------------------------------------------------- */
-#define APL_IN  19
+#define APL_IN  25
 #define APL_HID 256
 #define APL_OUT 3
 int64_t   apl_param_count(void);
-int32_t   apl_features(const float* S, int64_t n, int64_t ld, float scale, float* F /*n x 19*/,
-                       void* stream);
+/* F: device float [n x 25] out.  ws: apl_features_workspace_size(n) bytes
+ * (the neighbour lists between the two passes). */
+size_t    apl_features_workspace_size(int64_t n);
+int32_t   apl_features(const float* S, int64_t n, int64_t ld, float scale, float* F /*n x 25*/,
+                       void* ws, size_t ws_bytes, void* stream);
 int32_t   apl_targets(const float* R, const float* A, const int32_t* decisions, int64_t n,
                       int64_t ld, float scale, float* T /*n x 3*/, void* stream);
 size_t    apl_workspace_size(int64_t rows);

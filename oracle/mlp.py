@@ -2,10 +2,18 @@
 the model the CUDA library trains and evaluates).  TEST INFRASTRUCTURE ONLY.
 
 Per point k of a similarity matrix S with preference scale p > 0:
-  features (19): the 16 largest off-diagonal s(k,j) in decreasing order, the
-  mean and the standard deviation of the off-diagonal s(k,j), and s(k,k),
-  each divided by p;
-  network: 19 -> 256 -> 256 -> 3, ReLU after the two hidden layers;
+  features (25):
+    0-15  the 16 largest off-diagonal s(k,j) in decreasing order (ties: the
+          lower j first), divided by p;
+    16-17 the mean and the standard deviation of the off-diagonal s(k,j), / p;
+    18    s(k,k) / p;
+    19-22 log(1 + the number of j != k with s(k,j) >= -q p), q = 1/8, 1/4,
+          1/2, 1, the threshold -q p formed in float32 (p as float32);
+    23    D(k) - the largest D(j) over the 16 j of features 0-15, D = feature 20;
+    24    the fraction of those 16 j with D(j) > D(k);
+  (with fewer than 16 off-diagonal entries the last one is repeated, value
+  and index);
+  network: 25 -> 256 -> 256 -> 3, ReLU after the two hidden layers;
   outputs: (r_hat, a_hat, logit): predicted converged r(k,k)/p, a(k,k)/p and
   the log-odds that k is an exemplar;
   loss (mean over rows): (r_hat - t_r)^2 + (a_hat - t_a)^2
@@ -14,8 +22,8 @@ Per point k of a similarity matrix S with preference scale p > 0:
   bias correction.
 The network first standardises its input, x -> (x - mu) * isd, with mu and
 isd fixed (set from the training features, never updated by Adam).
-Parameters are one flat vector: W1 (256x19), b1, W2 (256x256), b2, W3 (3x256),
-b3, mu (19), isd (19).
+Parameters are one flat vector: W1 (256x25), b1, W2 (256x256), b2, W3 (3x256),
+b3, mu (25), isd (25).
 The matrix products may use bf16-rounded weights (``bf16=True``) to mirror
 the GPU, which keeps bf16 weights for its products and fp32 master weights.
 """
@@ -25,7 +33,7 @@ import numpy as np
 
 from . import ap
 
-IN, HID, OUT = 19, 256, 3
+IN, HID, OUT = 25, 256, 3
 SIZES = [("W1", (HID, IN)), ("b1", (HID,)), ("W2", (HID, HID)), ("b2", (HID,)),
          ("W3", (OUT, HID)), ("b3", (OUT,)), ("mu", (IN,)), ("isd", (IN,))]
 FIXED = ("mu", "isd")     # input standardisation, set from data, never trained
@@ -46,21 +54,34 @@ def pack(d):
 
 
 def row_features(S, scale):
-    """19 features per row of S (float64), divided by ``scale``."""
+    """25 features per row of S (float64); see the module docstring."""
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
-    off = ~np.eye(n, dtype=bool)
+    sc32 = np.float32(scale)
+    thr = [np.float64(np.float32(-(sc32 * np.float32(q)))) for q in (0.125, 0.25, 0.5, 1.0)]
     F = np.zeros((n, IN))
+    nbr = np.zeros((n, 16), dtype=np.int64)
     for k in range(n):
-        row = S[k][off[k]]
-        top = np.sort(row)[::-1][:16]
-        F[k, :top.size] = top
+        idx = np.array([j for j in range(n) if j != k])
+        row = S[k, idx]
+        order = np.lexsort((idx, -row))          # decreasing value, then increasing index
+        top, topi = row[order][:16], idx[order][:16]
         if top.size < 16:
-            F[k, top.size:] = top[-1] if top.size else 0.0
-        F[k, 16] = row.mean()
-        F[k, 17] = np.sqrt(max(0.0, (row ** 2).mean() - row.mean() ** 2))
-        F[k, 18] = S[k, k]
-    return F / scale
+            top = np.concatenate([top, np.full(16 - top.size, top[-1])])
+            topi = np.concatenate([topi, np.full(16 - topi.size, topi[-1])])
+        F[k, :16] = top / scale
+        nbr[k] = topi
+        F[k, 16] = row.mean() / scale
+        F[k, 17] = np.sqrt(max(0.0, (row ** 2).mean() - row.mean() ** 2)) / scale
+        F[k, 18] = S[k, k] / scale
+        for q, t in enumerate(thr):
+            F[k, 19 + q] = np.log1p(np.count_nonzero(row >= t))
+    D = F[:, 20]
+    for k in range(n):
+        Dn = D[nbr[k]]
+        F[k, 23] = D[k] - Dn.max()
+        F[k, 24] = np.count_nonzero(Dn > D[k]) / 16.0
+    return F
 
 
 def targets(R, A, scale):

@@ -114,29 +114,33 @@ class Batch:
         return p if p > 0 else 1.0
 
 
-def run(batch, R=None, A=None, damping=0.9, max_iter=1000, conv_iter=15):
+def run(batch, R=None, A=None, damping=0.9, max_iter=1000, conv_iter=15, ws=None):
     """Algorithm 1 on every problem of ``batch`` from (R, A) (zeros when
-    omitted): one batched sweep launch per iteration.  Returns (R, A,
-    per-problem results, device ms)."""
+    omitted): one batched sweep launch per iteration.  Every allocation
+    happens before the timed region.  Returns (R, A, per-problem results,
+    device ms)."""
     if R is None:
         R = torch.zeros_like(batch.S)
     if A is None:
         A = torch.zeros_like(batch.S)
+    if ws is None:
+        ws = capi.ap_iterate_batched_workspace(batch.n, batch.ld, batch.S.device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     res, _ = capi.ap_iterate_batched(batch.S, R, A, batch.off, batch.n, batch.ld,
-                                     damping=damping, max_iter=max_iter, conv_iter=conv_iter)
+                                     damping=damping, max_iter=max_iter, conv_iter=conv_iter, ws=ws)
     ev[1].record()
     torch.cuda.synchronize()
     return R, A, res, ev[0].elapsed_time(ev[1])
 
 
-def warm_start(batch, P, P16, gamma=1.0):
+def warm_start(batch, P, P16, gamma=1.0, R=None, A=None):
     """R0 = 0 and the network's column-constant A0 for every problem (features,
-    forward pass and warm start per problem), A0 scaled by ``gamma``.
+    forward pass and warm start per problem), A0 scaled by ``gamma``, into
+    (R, A) (allocated before the timed region when omitted).
     Returns (R, A, device ms)."""
-    R = torch.empty_like(batch.S)
-    A = torch.empty_like(batch.S)
+    R = torch.empty_like(batch.S) if R is None else R
+    A = torch.empty_like(batch.S) if A is None else A
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     for b in range(batch.count):

@@ -122,7 +122,8 @@ _SIGNATURES = {
     "lap_run": (C.c_int32, [_P, _I64, _I64, _I64, _I64, C.c_int32, _P, _P, C.c_uint64, C.c_int32,
                             C.POINTER(ApParams), _P, _P, C.POINTER(LapResult), _P, _SZ, _P]),
     "apl_param_count": (C.c_int64, []),
-    "apl_features": (C.c_int32, [_P, _I64, _I64, C.c_float, _P, _P]),
+    "apl_features_workspace_size": (_SZ, [_I64]),
+    "apl_features": (C.c_int32, [_P, _I64, _I64, C.c_float, _P, _P, _SZ, _P]),
     "apl_targets": (C.c_int32, [_P, _P, _P, _I64, _I64, C.c_float, _P, _P]),
     "apl_workspace_size": (_SZ, [_I64]),
     "apl_sync_bf16": (C.c_int32, [_P, _P, _P]),
@@ -323,8 +324,15 @@ def _i64_array(v):
     return (C.c_int64 * len(v))(*v)
 
 
+def ap_iterate_batched_workspace(n, ld, device):
+    """A workspace for ap_iterate_batched on problems of sizes n, ld."""
+    n_a, ld_a = _i64_array(n), _i64_array(ld)
+    return workspace(lib().ap_iterate_batched_workspace_size(C.cast(n_a, C.c_void_p),
+                                                             C.cast(ld_a, C.c_void_p), len(n)), device)
+
+
 def ap_iterate_batched(S, R, A, offsets, n, ld, damping=0.5, max_iter=200, conv_iter=15,
-                       check_every=0, decisions=False, stream=None):
+                       check_every=0, decisions=False, ws=None, stream=None):
     """Algorithm 1 on several problems stored in 1-D float32 arenas (CUDA
     tensors).  Problem b: n[b] x n[b] at element offset offsets[b], leading
     dimension ld[b].  Returns (list of result dicts, decisions or None)."""
@@ -336,8 +344,8 @@ def ap_iterate_batched(S, R, A, offsets, n, ld, damping=0.5, max_iter=200, conv_
     dec = torch.empty(sum(int(x) for x in n), dtype=torch.int32, device=S.device) if decisions else None
     p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
     out = (ApResult * count)()
-    ws = workspace(lib().ap_iterate_batched_workspace_size(C.cast(n_a, C.c_void_p),
-                                                           C.cast(ld_a, C.c_void_p), count), S.device)
+    if ws is None:
+        ws = ap_iterate_batched_workspace(n, ld, S.device)
     st = lib().ap_iterate_batched(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
                                   C.c_void_p(A.data_ptr()), C.cast(off_a, C.c_void_p),
                                   C.cast(n_a, C.c_void_p), C.cast(ld_a, C.c_void_p), count,
@@ -475,12 +483,17 @@ def apl_param_count():
     return int(lib().apl_param_count())
 
 
+APL_IN = 25
+
+
 def apl_features(S, scale, stream=None):
+    """The APL_IN per-point features of S (n x 25 float32)."""
     _dev_f32(S, "S")
     n = S.shape[0]
-    F = torch.empty((n, 19), dtype=torch.float32, device=S.device)
+    F = torch.empty((n, APL_IN), dtype=torch.float32, device=S.device)
+    ws = workspace(lib().apl_features_workspace_size(n), S.device)
     _check("apl_features", lib().apl_features(_ptr(S), n, S.stride(0), float(scale), _ptr(F),
-                                              _stream(stream)), ok=(AP_OK,))
+                                              _ptr(ws), ws.numel(), _stream(stream)), ok=(AP_OK,))
     return F
 
 

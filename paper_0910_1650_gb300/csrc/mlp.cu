@@ -2,15 +2,23 @@
 // 2's merged availabilities play, and its exemplar score can choose
 // Algorithm 3's landmarks).
 //
-// Per point k of S with preference scale p > 0, 19 features: the 16 largest
-// off-diagonal s(k,j) in decreasing order, the mean and standard deviation of
-// the off-diagonal s(k,j), and s(k,k), all divided by p.  A 19-256-256-3
-// network (ReLU) maps them to (r_hat, a_hat, logit): predicted converged
-// r(k,k)/p, a(k,k)/p and the exemplar log-odds.  Training: mean over rows of
-// (r_hat-t_r)^2 + (a_hat-t_a)^2 + softplus(logit) - t_e*logit, Adam.
+// Per point k of S with preference scale p > 0, 25 features:
+//   0-15  the 16 largest off-diagonal s(k,j), decreasing (ties: lower j first), / p
+//   16-17 mean and standard deviation of the off-diagonal s(k,j), / p
+//   18    s(k,k) / p
+//   19-22 log(1 + #{j != k : s(k,j) >= -q p}) for q = 1/8, 1/4, 1/2, 1 (the
+//         thresholds formed in float32): how many points lie within q times
+//         the preference scale, i.e. how much support k could collect
+//   23    D(k) - max_j D(j) over the 16 nearest j of k (those of features
+//         0-15), with D = feature 20: positive where k is denser than all of
+//         its neighbours, as exemplars tend to be
+//   24    the fraction of those 16 neighbours with D(j) > D(k)
+// A 25-256-256-3 network (ReLU) maps them to (r_hat, a_hat, logit): predicted
+// converged r(k,k)/p, a(k,k)/p and the exemplar log-odds.  Training: mean over
+// rows of (r_hat-t_r)^2 + (a_hat-t_a)^2 + softplus(logit) - t_e*logit, Adam.
 //
-// Parameters: one flat fp32 vector (W1 256x19, b1, W2 256x256, b2, W3 3x256,
-// b3, mu 19, isd 19); the input is standardised first, x -> (x - mu) * isd,
+// Parameters: one flat fp32 vector (W1 256x25, b1, W2 256x256, b2, W3 3x256,
+// b3, mu 25, isd 25); the input is standardised first, x -> (x - mu) * isd,
 // with mu and isd fixed (their gradient is zero, so Adam leaves them).  The
 // products use a bf16 copy of the weights with fp32 accumulation.  All
 // reductions (loss, weight gradients) run in a fixed order.
@@ -25,7 +33,8 @@
 namespace apgb {
 namespace mlp {
 
-constexpr int IN = 19, HID = 256, OUT = 3;
+constexpr int IN = 25, HID = 256, OUT = 3;
+constexpr int F_DENS = 20;       // the density D(k) of features 23-24
 constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
                   OFF_B2 = OFF_W2 + HID * HID, OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + OUT * HID,
                   OFF_MU = OFF_B3 + OUT, OFF_ISD = OFF_MU + IN, NP = OFF_ISD + IN;
@@ -33,28 +42,46 @@ constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
 // ---- features -------------------------------------------------------------------
 constexpr int TOPK = 16;
 
-__global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, float inv_scale,
-                                float* F) {
+// One block per row k (grid-stride): rows of S read once; per-thread sorted
+// top-16 (value, index) lists merged by 16 rounds of block arg-max ordered by
+// (value desc, index asc).  Writes features 0-22 and the 16 neighbour indices.
+__global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, float scale,
+                                float* F, int32_t* nbr) {
     __shared__ float hv[32];
-    __shared__ int ht[32];
+    __shared__ int hi[32];
     __shared__ double s1w[32], s2w[32];
+    __shared__ int cw[32][4];
     const int tid = threadIdx.x, lid = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const float inv_scale = 1.f / scale;
+    float thr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) thr[q] = -(scale * (0.125f * (float)(1 << q)));   // exact: powers of 2
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const float* row = S + (int64_t)k * ld;
         float top[TOPK];
+        int topi[TOPK];
 #pragma unroll
-        for (int q = 0; q < TOPK; ++q) top[q] = -INFINITY;
+        for (int q = 0; q < TOPK; ++q) { top[q] = -INFINITY; topi[q] = INT_MAX; }
         double s1 = 0.0, s2 = 0.0;
+        int cnt[4] = {0, 0, 0, 0};
         for (int j = tid; j < n; j += blockDim.x) {
             if (j == k) continue;
             const float v = row[j];
             s1 += v;
             s2 += (double)v * v;
-            if (v > top[TOPK - 1]) {            // insertion into the descending list
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cnt[q] += v >= thr[q];
+            if (v > top[TOPK - 1]) {            // insertion; equal values keep the lower j first
                 float x = v;
+                int xi = j;
 #pragma unroll
                 for (int q = 0; q < TOPK; ++q) {
-                    if (x > top[q]) { const float t = top[q]; top[q] = x; x = t; }
+                    if (x > top[q]) {
+                        const float t = top[q];
+                        const int ti = topi[q];
+                        top[q] = x; topi[q] = xi;
+                        x = t; xi = ti;
+                    }
                 }
             }
         }
@@ -63,51 +90,84 @@ __global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, 
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cnt[q] += __shfl_xor_sync(0xffffffffu, cnt[q], o);
         }
-        if (lid == 0) { s1w[wid] = s1; s2w[wid] = s2; }
+        if (lid == 0) {
+            s1w[wid] = s1; s2w[wid] = s2;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cw[wid][q] = cnt[q];
+        }
         // 16 rounds of block arg-max over each thread's next candidate
         int head = 0;
         float outv[TOPK];
+        int outi[TOPK];
         for (int r = 0; r < TOPK; ++r) {
             float v = head < TOPK ? top[head] : -INFINITY;
-            int who = tid;
+            int vi = head < TOPK ? topi[head] : INT_MAX;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const int w2 = __shfl_xor_sync(0xffffffffu, who, o);
-                if (v2 > v || (v2 == v && w2 < who)) { v = v2; who = w2; }
+                const int i2 = __shfl_xor_sync(0xffffffffu, vi, o);
+                if (v2 > v || (v2 == v && i2 < vi)) { v = v2; vi = i2; }
             }
-            if (lid == 0) { hv[wid] = v; ht[wid] = who; }
+            if (lid == 0) { hv[wid] = v; hi[wid] = vi; }
             __syncthreads();
             float bv = hv[0];
-            int bw = ht[0];
+            int bi = hi[0];
             for (int w = 1; w < nw; ++w)
-                if (hv[w] > bv || (hv[w] == bv && ht[w] < bw)) { bv = hv[w]; bw = ht[w]; }
-            if (tid == bw) ++head;
+                if (hv[w] > bv || (hv[w] == bv && hi[w] < bi)) { bv = hv[w]; bi = hi[w]; }
+            if (head < TOPK && bi != INT_MAX && topi[head] == bi) ++head;
             outv[r] = bv;
+            outi[r] = bi;
             __syncthreads();
         }
         if (tid == 0) {
             double t1 = 0.0, t2 = 0.0;
-            for (int w = 0; w < nw; ++w) { t1 += s1w[w]; t2 += s2w[w]; }
+            int c[4] = {0, 0, 0, 0};
+            for (int w = 0; w < nw; ++w) {
+                t1 += s1w[w]; t2 += s2w[w];
+                for (int q = 0; q < 4; ++q) c[q] += cw[w][q];
+            }
             const double m = t1 / (double)(n - 1);
             const double var = fmax(0.0, t2 / (double)(n - 1) - m * m);
             float* f = F + (int64_t)k * IN;
             float last = outv[0];
+            int lasti = outi[0];
             for (int r = 0; r < TOPK; ++r) {
-                if (outv[r] == -INFINITY) outv[r] = last;   // fewer than 16 off-diagonal values
+                if (outv[r] == -INFINITY) { outv[r] = last; outi[r] = lasti; }  // n - 1 < 16
                 last = outv[r];
+                lasti = outi[r];
                 f[r] = outv[r] * inv_scale;
+                nbr[(int64_t)k * TOPK + r] = outi[r];
             }
             f[16] = (float)(m * (double)inv_scale);
             f[17] = (float)(sqrt(var) * (double)inv_scale);
             f[18] = row[k] * inv_scale;
+            for (int q = 0; q < 4; ++q) f[19 + q] = log1pf((float)c[q]);
         }
         __syncthreads();
     }
 }
 
-// Fn = (F - mu) * isd, row-major [rows x 19].
+// Features 23-24 from the densities of each point's 16 neighbours.
+__global__ void neighbour_density_kernel(int n, const int32_t* __restrict__ nbr, float* F) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float d = F[(int64_t)k * IN + F_DENS];
+    float mx = -INFINITY;
+    int denser = 0;
+#pragma unroll
+    for (int q = 0; q < TOPK; ++q) {
+        const float dj = F[(int64_t)nbr[(int64_t)k * TOPK + q] * IN + F_DENS];
+        mx = fmaxf(mx, dj);
+        denser += dj > d;
+    }
+    F[(int64_t)k * IN + 23] = d - mx;
+    F[(int64_t)k * IN + 24] = (float)denser * (1.f / TOPK);
+}
+
+// Fn = (F - mu) * isd, row-major [rows x IN].
 __global__ void standardise_kernel(const float* __restrict__ F, int rows,
                                    const float* __restrict__ P, float* Fn) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -365,13 +425,24 @@ using namespace apgb::mlp;
 
 APGB_API int64_t apl_param_count(void) { return NP; }
 
+APGB_API size_t apl_features_workspace_size(int64_t n) {
+    if (n < 2 || n > INT_MAX) return 0;
+    Carver c(nullptr);
+    c.take<int32_t>((size_t)n * TOPK);
+    return c.used;
+}
+
 APGB_API int32_t apl_features(const float* S, int64_t n, int64_t ld, float scale, float* F,
-                              void* stream) {
+                              void* ws, size_t ws_bytes, void* stream) {
     if (!S || !F || n < 2 || ld < n || n > INT_MAX || !(scale > 0.f)) return AP_ERR_INVALID_ARG;
     AP_TRY(require_sm103());
+    AP_TRY(check_ws(ws, ws_bytes, apl_features_workspace_size(n)));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    features_kernel<<<(int)std::min<int64_t>(n, 65535), 256, 0, s>>>(S, (int)n, ld, 1.f / scale, F);
-    note_launches(1);
+    Carver c(ws);
+    int32_t* nbr = c.take<int32_t>((size_t)n * TOPK);
+    features_kernel<<<(int)std::min<int64_t>(n, 65535), 256, 0, s>>>(S, (int)n, ld, scale, F, nbr);
+    neighbour_density_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, nbr, F);
+    note_launches(2);
     return last_error();
 }
 
@@ -479,7 +550,8 @@ struct RunWs {
 
 static size_t carve_run(void* ws, int64_t n, int64_t ld, RunWs* w) {
     const size_t mb = apl_workspace_size(n);
-    const size_t sb = std::max(ap_iterate_workspace_size(n, ld), exemplars_ws_bytes(n));
+    const size_t sb = std::max({ap_iterate_workspace_size(n, ld), exemplars_ws_bytes(n),
+                                apl_features_workspace_size(n)});
     Carver c(ws);
     w->F = c.take<float>((size_t)n * mlp::IN);
     w->Y = c.take<float>((size_t)n * mlp::OUT);
@@ -522,7 +594,7 @@ APGB_API int32_t apl_ap_run(const float* S, int64_t n, int64_t ld, const float* 
 
     *out = apl_result{};
     AP_CUDA_TRY(cudaEventRecord(ev[0], s));
-    AP_TRY(apl_features(S, n, ld, scale, w.F, stream));
+    AP_TRY(apl_features(S, n, ld, scale, w.F, w.sub_ws, w.sub_bytes, stream));
     AP_CUDA_TRY(cudaEventRecord(ev[1], s));
     AP_TRY(apl_forward(P, P16, w.F, n, w.Y, w.mlp_ws, w.mlp_bytes, stream));
     AP_TRY(apl_warm_start(w.Y, n, scale, R, A, ld, stream));

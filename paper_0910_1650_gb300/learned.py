@@ -78,3 +78,27 @@ def mixture_problems(count, lo=500, hi=2000, d=32, seed=synth.SEED_BASE + 300, o
         X, _ = synth.gaussian_mixture(int(sizes[b]), d, k, seed + 1000 + b, 4.0, 1.0)
         out.append(X)
     return out
+
+
+def landmark_training_problems(count=12, n=4000, d=128, clusters=100, seed=synth.SEED_BASE + 400):
+    """Mixtures with the landmark pool's density (about 40 points per
+    cluster; 1000-cluster workload, sigma 0.5, centres N(0, 16 I))."""
+    return [synth.gaussian_mixture(n, d, clusters, seed + b, 4.0, 0.5, False)[0]
+            for b in range(count)]
+
+
+def landmark_scores(X, n_landmarks, P, P16, seed=synth.SEED_BASE + 401, pool_factor=2):
+    """Scores for Algorithm 3's landmark choice by the network's exemplar
+    log-odds: a uniform pool of pool_factor * n_landmarks points (seeded
+    permutation) gets its own S, features and forward pass; every other
+    point scores -inf, so lap_run(mode="score") keeps the best-scoring
+    n_landmarks of the pool.  Returns a device float32 [n] tensor."""
+    n = X.shape[0]
+    m = min(n, pool_factor * int(n_landmarks))
+    pool = torch.from_numpy(synth.Stream(seed, 0).permutation(n)[:m].copy()).to(X.device)
+    S, p = capi.ap_similarity(X[pool].contiguous(), precision="bf16")
+    F = capi.apl_features(S, abs(p) if p != 0 else 1.0)
+    Y = capi.apl_forward(P, P16, F)
+    score = torch.full((n,), float("-inf"), dtype=torch.float32, device=X.device)
+    score[pool] = Y[:, 2]
+    return score

@@ -236,7 +236,7 @@ def workload(c: int, scale: float = 1.0):
     raise ValueError(c)
 
 
-def mlp_init(seed: int = SEED_BASE + 77, n_in: int = 19, hid: int = 256, n_out: int = 3):
+def mlp_init(seed: int = SEED_BASE + 77, n_in: int = 25, hid: int = 256, n_out: int = 3):
     """Initial parameters of the warm-start network as one float32 vector
     (W1, b1, W2, b2, W3, b3, mu, isd): He-normal weights N(0, 2/fan_in), zero
     biases, identity input standardisation (mu = 0, isd = 1)."""

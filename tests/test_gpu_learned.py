@@ -43,13 +43,18 @@ def test_features_match_oracle(n):
     scale = abs(float(np.float32(oap.offdiag_median(S))))
     F = capi.apl_features(_square(S), scale).cpu().numpy().astype(np.float64)
     Fo = omlp.row_features(S, scale)
+    assert F.shape == (n, 25)
     assert np.abs(F[:, :16] - Fo[:, :16]).max() <= 2e-7 * np.abs(Fo[:, :16]).max()
-    assert rel_inf(F[:, 16:], Fo[:, 16:]) <= 1e-6
+    assert rel_inf(F[:, 16:19], Fo[:, 16:19]) <= 1e-6
+    # counts are integers compared in float32 on both sides; logs in float32
+    assert np.abs(F[:, 19:23] - Fo[:, 19:23]).max() <= 1e-6
+    assert np.abs(F[:, 23] - Fo[:, 23]).max() <= 2e-6
+    assert np.array_equal(F[:, 24], Fo[:, 24])
 
 
 def test_forward_matches_oracle():
     P, Pd, P16 = _params()
-    F = np.random.default_rng(7).normal(size=(1000, 19)).astype(np.float32)
+    F = np.random.default_rng(7).normal(size=(1000, 25)).astype(np.float32)
     Y = capi.apl_forward(Pd, P16, torch.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
     Yo, _ = omlp.forward(P, F.astype(np.float64), bf16=True)
     assert rel_inf(Y, Yo) <= 1e-4
@@ -59,7 +64,7 @@ def test_gradient_matches_oracle_and_adam_step():
     P, Pd, P16 = _params(5)
     g = np.random.default_rng(8)
     rows = 777
-    F = g.normal(size=(rows, 19)).astype(np.float32)
+    F = g.normal(size=(rows, 25)).astype(np.float32)
     T = np.stack([g.normal(size=rows), np.abs(g.normal(size=rows)), (g.random(rows) < 0.2)],
                  1).astype(np.float32)
     M = torch.zeros_like(Pd)
@@ -117,3 +122,29 @@ def test_training_and_what_the_network_gains(capsys):
         print(f"\nlearned warm start: loss {losses[0]:.4f} -> {losses[-1]:.4f}; held-out "
               f"iterations warm {warm:.1f} vs cold {cold:.1f} (x{cold / warm:.2f}); "
               f"warm result kept on {used:.0%} of problems")
+
+
+def test_learned_landmark_scores_pick_from_the_pool():
+    """landmark_scores: a seeded uniform pool of 2L points is scored by the
+    network (features of the pool's own S), every other point scores -inf,
+    and lap_run in score mode takes the L best of the pool."""
+    X, _ = synth.gaussian_mixture(3000, 16, 30, 42, 4.0, 0.5, False)
+    P, Pd, P16 = _params(11)
+    Xd = torch.from_numpy(X).cuda()
+    L = 300
+    score = learned.landmark_scores(Xd, L, Pd, P16)
+    sc = score.cpu().numpy()
+    pool = np.isfinite(sc)
+    assert pool.sum() == 2 * L
+    # the pool's scores are the network's log-odds on the pool's own features
+    # (same seeded pool order as inside landmark_scores, so the same bits)
+    perm = synth.Stream(synth.SEED_BASE + 401, 0).permutation(X.shape[0])[:2 * L]
+    assert np.array_equal(np.sort(perm), np.nonzero(pool)[0])
+    Sp, p = capi.ap_similarity(Xd[torch.from_numpy(perm.copy()).cuda()].contiguous(), precision="bf16")
+    Y = capi.apl_forward(Pd, P16, capi.apl_features(Sp, abs(p))).cpu().numpy()
+    assert np.array_equal(sc[perm], Y[:, 2])
+    idx, lm, _ = capi.lap_run(Xd, L, "score", score=score, damping=0.9, max_iter=50, conv_iter=10)
+    lm = np.sort(lm.cpu().numpy())
+    best = np.sort(np.lexsort((np.arange(sc.size), -sc.astype(np.float64)))[:L])
+    assert np.array_equal(lm, best)
+    assert pool[lm].all()

@@ -16,7 +16,7 @@ def _problem(seed=0, n=40):
 
 
 def test_parameter_count_and_layout():
-    assert mlp.NP == 256 * 19 + 256 + 256 * 256 + 256 + 3 * 256 + 3 + 2 * 19
+    assert mlp.NP == 256 * 25 + 256 + 256 * 256 + 256 + 3 * 256 + 3 + 2 * 25
     P = synth.mlp_init()
     assert P.size == mlp.NP
     d = mlp.unpack(P)
@@ -33,6 +33,27 @@ def test_features_hand_row():
     assert F[0, 16] == -1.0                      # mean of -1, -9 is -5, over 5
     assert abs(F[0, 17] - 0.8) < 1e-15           # std of -1, -9 is 4, over 5
     assert F[0, 18] == -1.0
+
+
+def test_density_features_hand_example():
+    """Four points on a line at 0, 1, 2, 10 (s = -squared distance), scale 8:
+    thresholds -1, -2, -4, -8.  Counts, neighbour lists and density
+    contrasts worked out by hand."""
+    x = np.array([0.0, 1.0, 2.0, 10.0])
+    S = -(x[:, None] - x[None, :]) ** 2
+    np.fill_diagonal(S, -30.0)
+    F = mlp.row_features(S, 8.0)
+    l = np.log1p
+    counts = {0: (1, 1, 2, 2), 1: (2, 2, 2, 2), 2: (1, 1, 2, 2), 3: (0, 0, 0, 0)}
+    for k, c in counts.items():
+        assert np.allclose(F[k, 19:23], l(np.array(c, dtype=float)), rtol=0, atol=1e-15)
+    D = [l(1), l(2), l(1), l(0)]
+    assert abs(F[0, 23] - (D[0] - D[1])) < 1e-15 and F[0, 24] == 1 / 16     # neighbours 1, 2, 3 x14
+    assert abs(F[1, 23] - (D[1] - D[0])) < 1e-15 and F[1, 24] == 0.0        # 0, 2 (tie: lower j), 3
+    assert abs(F[2, 23] - (D[2] - D[1])) < 1e-15 and F[2, 24] == 1 / 16     # 1, 0, 3 x14
+    assert abs(F[3, 23] - (D[3] - D[1])) < 1e-15 and F[3, 24] == 1.0        # 2, 1, 0 x14
+    # the top-16 values of row 1 keep both -1 entries (ties) then pad with -81
+    assert np.array_equal(F[1, :4], np.array([-1, -1, -81, -81]) / 8.0)
 
 
 @pytest.mark.parametrize("bf16", [False, True])
