@@ -478,11 +478,19 @@ def time_to_converge(dev):
                                                    precision="bf16", damping=DAMPING,
                                                    max_iter=MAX_ITER, conv_iter=CONV_ITER))
     lrn = lap_learned(Xs)
+    (_, _, lf), t_full = timed(lambda: capi.lap_run_full(Xs, 20000, 20000, seed=synth.config_seed(3),
+                                                         precision="bf16", damping=DAMPING,
+                                                         max_iter=MAX_ITER, conv_iter=CONV_ITER))
     out["lap"] = {
         "workload": "1000 Gaussians in R^128 (sigma 0.5, centres N(0,16I)); 20000 uniform landmarks; "
                     "learned: the 20000 best exemplar scores of a 40000-point uniform pool",
         "scorer_training": {"problems": 12, "rows": int(Fl.shape[0]), "loss_first": round(ll[0], 4),
                             "loss_last": round(ll[-1], 4), "wall_s": round(train_s, 1)},
+        "lap_steps_1_4": {"ms": round(t_full, 1), "levels": lf["levels"], "base_case": lf["base_case"],
+                          "unassigned": lf["unassigned"], "exemplars_at": lf["exemplars_at"],
+                          "n_exemplars": lf["n_exemplars"], "netsim": lf["netsim"],
+                          "time_ratio_plain_over_lap": round(t_plain / t_full, 3),
+                          "netsim_rel_diff": (lf["netsim"] - exp_["netsim"]) / abs(exp_["netsim"])},
         "lap_learned": dict(lrn, time_ratio_plain_over_lap=round(t_plain / lrn["ms"], 3),
                             netsim_rel_diff=(lrn["netsim"] - exp_["netsim"]) / abs(exp_["netsim"])),
         "full_1e6": full,

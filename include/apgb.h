@@ -280,6 +280,50 @@ int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_l
                   void* stream);
 
 /* ---------------------------------------------------------------------------
+ * lap_run_full -- Algorithm 3 (Section 4), Steps 1-4:
+ *  Step 1  L uniform landmarks (the L points with the smallest splitmix64 keys
+ *          of seed + level, ties by index), Algorithm 1 on their S; the
+ *          preference is the off-diagonal median of the first level's landmark
+ *          S and is kept at every later level and in Step 3.
+ *  Step 2  max_distance(j) = the largest squared distance from a landmark of
+ *          class j to its exemplar (from the landmark S); every other point
+ *          joins its nearest exemplar's class when its squared distance to it
+ *          (bf16-rounded features centred on the level's mean, fp32
+ *          accumulation, as in lap_run) is below that class's max_distance.
+ *  Step 3  the m points left: Algorithm 1 on them when m <= m0 (one point is
+ *          its own exemplar); else Steps 1-3 on them (the next level, up to
+ *          max_levels levels; points still left after the last level join
+ *          their nearest exemplar in Step 4).  Exemplars of every level merge.
+ *  Step 4  every point joins its nearest exemplar of the merged set
+ *          (refinement by reassignment); exemplars keep themselves.
+ *  X          device float32 [n x ldx]; n_landmarks (L) in [2, n]; m0 in
+ *             [2, n]; max_levels in [1, AP_LAP_MAX_LEVELS].
+ *  idx        device int32[n] out: each point's exemplar.
+ *  level_of   device int32[n] out (may be NULL): the level whose Step 2 (or
+ *             Step 3's Algorithm 1) settled the point, -1 if none did.
+ *  out        host lap_full_result*.  The call synchronises ``stream``.
+ *  Errors: AP_NO_EXEMPLARS when the first level's landmarks give none (idx
+ *  = -1); AP_ERR_TOO_LARGE if the merged set outgrows min(n, L*max_levels+m0).
+ * ------------------------------------------------------------------------- */
+#define AP_LAP_MAX_LEVELS 8
+typedef struct lap_full_result {
+    int32_t levels;                          /* levels whose Steps 1-2 ran       */
+    int32_t n_exemplars;                     /* size of the merged set           */
+    float   pref;
+    int32_t base_case;                       /* 1: Step 3 ended in Algorithm 1   */
+    int32_t unassigned[AP_LAP_MAX_LEVELS];   /* points left by each level's gate */
+    int32_t exemplars_at[AP_LAP_MAX_LEVELS + 1];
+    float   ms;                              /* device time of the call          */
+    double  dpsim, expref, netsim;
+} lap_full_result;
+size_t    lap_run_full_workspace_size(int64_t n, int64_t d, int64_t n_landmarks, int64_t m0,
+                                      int32_t max_levels);
+int32_t   lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_landmarks,
+                       int64_t m0, uint64_t seed, int32_t precision, const ap_params* params,
+                       int32_t max_levels, int32_t* idx, int32_t* level_of,
+                       lap_full_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned warm start.  The paper has no learned part: this network plays the
  * role of Algorithm 2's merged availabilities (a warm start for Algorithm 1)
  * and its exemplar score can choose Algorithm 3's landmarks (the non-uniform

@@ -56,3 +56,115 @@ def run(X, landmarks, lam=0.5, max_iter=200, convits=15, pref="median"):
     expref = float(p * E.size) if np.isscalar(p) else float(np.sum(p))
     return dict(landmarks=landmarks, S_L=S_L, pref=p, landmark_run=res, E=E,
                 idx=idx, dpsim=dpsim, expref=expref, netsim=dpsim + expref)
+
+
+# ---- Algorithm 3, Steps 1-4 ------------------------------------------------------------
+
+def _rounded_points(X):
+    """The bf16-rounded centred points on which the GPU takes its distance
+    decisions (the level's own mean), as float64."""
+    return ap.similarity_bf16_inputs(X)
+
+
+def _sqdist(A, B):
+    return ((A[:, None, :] - B[None, :, :]) ** 2).sum(axis=2)
+
+
+def run_full(X, n_landmarks, seed, m0, lam=0.5, max_iter=200, convits=15, max_levels=8):
+    """Algorithm 3 Steps 1-4 (Section 4), literally:
+
+    Step 1  uniform landmarks (``uniform_landmarks`` with the level's seed),
+            Algorithm 1 on their S (preference: the off-diagonal median of the
+            first level's landmark S, kept at every level) -> c classes.
+    Step 2  max_distance(j) = the largest squared distance from a landmark of
+            class j to its exemplar (from the landmark S); every other point i
+            joins class j = its nearest exemplar when distance(i, c_j) <
+            max_distance(j), else stays unassigned.
+    Step 3  the m unassigned points: Algorithm 1 on them when m <= m0 (one
+            point is its own exemplar), else Steps 1-3 on them recursively
+            (seed + level); their exemplars join the set.
+    Step 4  every point is reassigned to its nearest exemplar of the merged
+            set; exemplars keep themselves.
+
+    Readings: distances are squared Euclidean (the negative of s); the nearest
+    exemplar and the gate are decided on the bf16-rounded centred points of
+    the level (the precision of the tensor-core assignment), lowest index on
+    ties; max_distance comes from the landmark S.
+    Returns dict(E, idx, levels (list of per-level dicts), pref, dpsim,
+    expref, netsim)."""
+    X = np.asarray(X, dtype=np.float32)
+    n = X.shape[0]
+    ids = np.arange(n)
+    E_all = []
+    levels = []
+    p = None
+    level = 0
+    while True:
+        Xl = X[ids]
+        nl = Xl.shape[0]
+        if level > 0 and nl <= m0:
+            # Step 3 base case: Algorithm 1 on the remaining points
+            if nl == 1:
+                E_all.append(ids[:1])
+                levels.append(dict(n=1, E=ids[:1], unassigned=np.zeros(0, dtype=np.int64)))
+            else:
+                S_m, _ = ap.build_similarity(Xl, pref=p)
+                res = ap.run(S_m, lam, max_iter, convits)
+                ex = ap.exemplars(S_m, res["R"], res["A"])
+                E_all.append(ids[ex["E"]])
+                levels.append(dict(n=nl, E=ids[ex["E"]], unassigned=np.zeros(0, dtype=np.int64)))
+            break
+        L = min(n_landmarks, nl)
+        lm = uniform_landmarks(nl, L, seed + level)
+        S_L, pl = ap.build_similarity(Xl[lm], pref="median" if p is None else p)
+        if p is None:
+            p = pl
+        res = ap.run(S_L, lam, max_iter, convits)
+        ex = ap.exemplars(S_L, res["R"], res["A"])
+        if ex["E"].size == 0:
+            levels.append(dict(n=nl, E=np.zeros(0, dtype=np.int64), unassigned=ids))
+            break
+        cls = ex["idx"]                                  # landmark position -> exemplar position
+        Epos = ex["E"]
+        slot = {int(e): j for j, e in enumerate(Epos)}
+        maxd = np.zeros(Epos.size)
+        for i in range(L):
+            j = slot[int(cls[i])]
+            maxd[j] = max(maxd[j], -S_L[i, cls[i]] if i != cls[i] else 0.0)
+        Xr = _rounded_points(Xl)
+        E_loc = lm[Epos]
+        D = _sqdist(Xr, Xr[E_loc])
+        near = np.argmin(D, axis=1)                      # first minimum: lowest exemplar position
+        dmin = D[np.arange(nl), near]
+        is_lm = np.zeros(nl, dtype=bool)
+        is_lm[lm] = True
+        ok = is_lm | (dmin < maxd[near])
+        srt = np.sort(D, axis=1)
+        gap = srt[:, 1] - srt[:, 0] if srt.shape[1] > 1 else np.full(nl, np.inf)
+        margin = np.abs(dmin - maxd[near])
+        E_all.append(ids[E_loc])
+        un = ids[~ok]
+        levels.append(dict(n=nl, L=L, E=ids[E_loc], maxd=maxd, unassigned=un,
+                           margin=margin[~is_lm], gap=gap[~is_lm], scale=maxd.max() if maxd.size else 0.0))
+        if un.size == 0 or level + 1 >= max_levels:
+            break
+        ids = un
+        level += 1
+    E = np.unique(np.concatenate(E_all)) if E_all else np.zeros(0, dtype=np.int64)
+    if E.size == 0:
+        return dict(E=E, idx=np.full(n, -1), levels=levels, pref=p, dpsim=np.nan,
+                    expref=np.nan, netsim=np.nan)
+    # Step 4: nearest exemplar of the merged set, on the whole set's rounded points
+    Xr = _rounded_points(X)
+    D = _sqdist(Xr, Xr[E])
+    idx = E[np.argmin(D, axis=1)]
+    idx[E] = E
+    srt = np.sort(D, axis=1)
+    gap4 = srt[:, 1] - srt[:, 0] if srt.shape[1] > 1 else np.full(n, np.inf)
+    is_ex = np.zeros(n, dtype=bool)
+    is_ex[E] = True
+    s_ic = -((X[~is_ex].astype(np.float64) - X[idx[~is_ex]].astype(np.float64)) ** 2).sum(axis=1)
+    dpsim = float(s_ic.sum())
+    expref = float(p * E.size)
+    return dict(E=E, idx=idx, levels=levels, pref=p, gap=gap4, dpsim=dpsim, expref=expref,
+                netsim=dpsim + expref)

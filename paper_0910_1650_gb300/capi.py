@@ -77,6 +77,22 @@ class LapResult(C.Structure):
         return d
 
 
+AP_LAP_MAX_LEVELS = 8
+
+
+class LapFullResult(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("n_exemplars", C.c_int32), ("pref", C.c_float),
+                ("base_case", C.c_int32), ("unassigned", C.c_int32 * AP_LAP_MAX_LEVELS),
+                ("exemplars_at", C.c_int32 * (AP_LAP_MAX_LEVELS + 1)), ("ms", C.c_float),
+                ("dpsim", C.c_double), ("expref", C.c_double), ("netsim", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["unassigned"] = list(self.unassigned)[:max(self.levels, 1)]
+        d["exemplars_at"] = list(self.exemplars_at)[:self.levels + self.base_case]
+        return d
+
+
 class AplResult(C.Structure):
     _fields_ = [("used_warm", C.c_int32), ("warm_iters", C.c_int32), ("cold_iters", C.c_int32),
                 ("pad", C.c_int32), ("warm_netsim", C.c_double), ("cold_netsim", C.c_double),
@@ -121,6 +137,10 @@ _SIGNATURES = {
     "lap_run_workspace_size": (_SZ, [_I64, _I64, _I64]),
     "lap_run": (C.c_int32, [_P, _I64, _I64, _I64, _I64, C.c_int32, _P, _P, C.c_uint64, C.c_int32,
                             C.POINTER(ApParams), _P, _P, C.POINTER(LapResult), _P, _SZ, _P]),
+    "lap_run_full_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, C.c_int32]),
+    "lap_run_full": (C.c_int32, [_P, _I64, _I64, _I64, _I64, _I64, C.c_uint64, C.c_int32,
+                                 C.POINTER(ApParams), C.c_int32, _P, _P, C.POINTER(LapFullResult),
+                                 _P, _SZ, _P]),
     "apl_param_count": (C.c_int64, []),
     "apl_features_workspace_size": (_SZ, [_I64]),
     "apl_features": (C.c_int32, [_P, _I64, _I64, C.c_float, _P, _P, _SZ, _P]),
@@ -405,6 +425,26 @@ def lap_run(X, n_landmarks, mode="uniform", score=None, landmarks=None, seed=0, 
                        C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
     _check("lap_run", st)
     return idx, lm, res.as_dict()
+
+
+def lap_run_full(X, n_landmarks, m0, seed=0, precision="fp32", damping=0.5, max_iter=200,
+                 conv_iter=15, max_levels=AP_LAP_MAX_LEVELS, check_every=0, stream=None):
+    """Algorithm 3 Steps 1-4 on features X (n x d).  Returns (idx, level_of,
+    result dict)."""
+    _dev_f32(X, "X")
+    n, d = X.shape
+    idx = torch.empty(n, dtype=torch.int32, device=X.device)
+    level_of = torch.empty(n, dtype=torch.int32, device=X.device)
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    res = LapFullResult()
+    ws = workspace(lib().lap_run_full_workspace_size(n, d, int(n_landmarks), int(m0), int(max_levels)),
+                   X.device)
+    prec = {"fp32": AP_PREC_FP32, "bf16": AP_PREC_BF16}[precision]
+    st = lib().lap_run_full(_ptr(X), n, d, X.stride(0), int(n_landmarks), int(m0),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, prec, C.byref(p), int(max_levels), _ptr(idx),
+                            _ptr(level_of), C.byref(res), _ptr(ws), ws.numel(), _stream(stream))
+    _check("lap_run_full", st)
+    return idx, level_of, res.as_dict()
 
 
 def ap_sweep_get_config(n):

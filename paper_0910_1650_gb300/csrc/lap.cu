@@ -271,6 +271,123 @@ __global__ void sum_f64_kernel(const double* __restrict__ v, int64_t n, double* 
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// ---- Steps 2-4 of the full algorithm ------------------------------------------------
+// flags[rows[j]] = 1
+__global__ void flag_rows_kernel(const int32_t* __restrict__ rows, int64_t m, int32_t* flags) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x)
+        flags[rows[j]] = 1;
+}
+
+// slot[j] = rank of landmark position j among the exemplar positions
+// (idxL[j] == j), ascending -- the order landmark_exemplars_kernel lists them.
+__global__ void exemplar_slots_kernel(const int32_t* __restrict__ idxL, int64_t L, int32_t* slot) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t lo = 0; lo < L; lo += blockDim.x) {
+        const int64_t j = lo + threadIdx.x;
+        const bool f = j < L && idxL[j] == (int32_t)j;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lid == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < wid; ++w) before += wsum[w];
+        if (f) slot[j] = base + before + __popc(bal & ((1u << lid) - 1u));
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += wsum[w];
+            base += t;
+        }
+        __syncthreads();
+    }
+}
+
+// max_distance of each class (bit pattern of a float >= 0, so unsigned max
+// is float max): the largest -s(i, e) over the landmarks i of the class of e.
+__global__ void max_distance_kernel(const float* __restrict__ SL, int64_t ldL,
+                                    const int32_t* __restrict__ idxL, const int32_t* __restrict__ slot,
+                                    int64_t L, unsigned* maxd) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int32_t e = idxL[i];
+    const float d = (i == e) ? 0.f : fmaxf(0.f, -SL[i * ldL + e]);
+    atomicMax(&maxd[slot[e]], __float_as_uint(d));
+}
+
+// Step 2's gate: point i stays unassigned unless it is a landmark or its
+// squared distance to its nearest exemplar, |x_i|^2 - best_i on the rounded
+// centred points, is below that class's max_distance.  Assigned points get
+// their level.
+__global__ void gate_kernel(int64_t nl, const int32_t* __restrict__ arg,
+                            const float* __restrict__ best, const float* __restrict__ xnrm,
+                            const unsigned* __restrict__ maxd, const int32_t* __restrict__ is_lm,
+                            const int32_t* __restrict__ ids, int32_t level, int32_t* un,
+                            int32_t* level_of) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = is_lm[i] || (xnrm[i] - best[i]) < __uint_as_float(maxd[arg[i]]);
+        un[i] = ok ? 0 : 1;
+        if (ok && level_of) level_of[ids ? ids[i] : i] = level;
+    }
+}
+
+// out = the indices i < n with flags[i] != 0, ascending; *count their number.
+__global__ void compact_flags_kernel(const int32_t* __restrict__ flags, int64_t n, int32_t* out,
+                                     int32_t* count) {
+    __shared__ int wsum[32];
+    __shared__ int64_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t lo = 0; lo < n; lo += blockDim.x) {
+        const int64_t i = lo + threadIdx.x;
+        const bool f = i < n && flags[i] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lid == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < wid; ++w) before += wsum[w];
+        if (f) out[base + before + __popc(bal & ((1u << lid) - 1u))] = (int32_t)i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += wsum[w];
+            base += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = (int32_t)base;
+}
+
+// out[j] = ids[local[j]] (ids == NULL: the identity); level_of of those set.
+__global__ void map_ids_kernel(const int32_t* __restrict__ local, int64_t m,
+                               const int32_t* __restrict__ ids, int32_t* out, int32_t level,
+                               int32_t* level_of) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = ids ? ids[local[j]] : local[j];
+        out[j] = g;
+        if (level_of) level_of[g] = level;
+    }
+}
+
+__global__ void set_level_kernel(const int32_t* __restrict__ ids, int64_t m, int32_t level,
+                                 int32_t* level_of) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x)
+        level_of[ids[j]] = level;
+}
+
+__global__ void fill_i32_kernel(int32_t* p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 // ---- workspace ------------------------------------------------------------------------
 struct LapWs {
     uint64_t* keys;
@@ -475,4 +592,276 @@ APGB_API int32_t lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int6
     out->expref = (double)pref * c;
     out->netsim = out->dpsim + out->expref;
     return (params->conv_iter > 0 && !lc) ? AP_NOT_CONVERGED : AP_OK;
+}
+
+// ---- Algorithm 3, Steps 1-4 --------------------------------------------------------------
+namespace apgb {
+
+struct LapFullWs {
+    LapWs lap;                  // one level's Steps 1-2 (sized for n points)
+    float* Xn[2];               // features of the points left, compacted (n x d each)
+    int32_t* ids[2];            // their indices in X
+    int32_t *is_lm, *un, *list, *cnt, *slot;
+    unsigned* maxd;
+    float *best, *xnrm;
+    int32_t* E;                 // merged exemplar set (indices in X)
+    __nv_bfloat16* Eb;
+    float* enrm;
+    float *Sm, *Rm, *Am;        // Step 3's Algorithm 1 on at most m0 points
+    int32_t* idxm;
+    void* sub;
+    size_t sub_bytes;
+    int64_t emax;
+};
+
+static size_t carve_lap_full(void* ws, int64_t n, int64_t d, int64_t L, int64_t m0,
+                             int32_t max_levels, LapFullWs* w) {
+    const int dpad = (int)((d + 63) / 64 * 64);
+    const int64_t npad = (n + 127) / 128 * 128;
+    const int64_t emax = std::min<int64_t>(n, L * max_levels + m0);
+    const int64_t epad = (emax + 255) / 256 * 256;
+    const int64_t ldm = ld32(m0);
+    const size_t sub = std::max({ap_similarity_workspace_size(m0, d), ap_iterate_workspace_size(m0, ldm),
+                                 exemplars_ws_bytes(m0)});
+    LapWs tmp;
+    const size_t lap_bytes = carve_lap(nullptr, n, d, L, &tmp);
+    Carver c(ws);
+    char* lap_base = c.take<char>(lap_bytes);
+    if (ws) carve_lap(lap_base, n, d, L, &w->lap);
+    for (int b = 0; b < 2; ++b) w->Xn[b] = c.take<float>((size_t)n * d);
+    for (int b = 0; b < 2; ++b) w->ids[b] = c.take<int32_t>(n);
+    w->is_lm = c.take<int32_t>(n);
+    w->un = c.take<int32_t>(n);
+    w->list = c.take<int32_t>(n);
+    w->cnt = c.take<int32_t>(1);
+    w->slot = c.take<int32_t>(L);
+    w->maxd = c.take<unsigned>(L);
+    w->best = c.take<float>(n);
+    w->xnrm = c.take<float>(npad);
+    w->E = c.take<int32_t>(emax);
+    w->Eb = c.take<__nv_bfloat16>((size_t)epad * dpad);
+    w->enrm = c.take<float>(epad);
+    w->Sm = c.take<float>((size_t)m0 * ldm);
+    w->Rm = c.take<float>((size_t)m0 * ldm);
+    w->Am = c.take<float>((size_t)m0 * ldm);
+    w->idxm = c.take<int32_t>(m0);
+    w->sub = c.take<char>(sub);
+    w->sub_bytes = sub;
+    w->emax = emax;
+    return (lap_bytes && sub) ? c.used : 0;
+}
+
+static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+// Algorithm 1 on the landmarks of one level: S (median preference the first
+// time, then the kept preference), iterations, exemplars.  Returns the
+// exemplar count (0: none) or a negative status.
+static int32_t landmark_ap(const LapWs& w, int64_t L, int64_t d, int32_t precision,
+                           const ap_params* params, bool have_p, float* p, cudaStream_t s) {
+    const int64_t ldL = ld32(L);
+    AP_TRY(ap_similarity(w.XL, L, d, d, w.SL, ldL, precision, have_p ? AP_PREF_SCALAR : AP_PREF_MEDIAN,
+                         have_p ? p : nullptr, 0.0, 0, have_p ? nullptr : p, w.sub_ws, w.sub_bytes, s));
+    AP_CUDA_TRY(cudaMemset2DAsync(w.RL, ldL * sizeof(float), 0, L * sizeof(float), L, s));
+    AP_CUDA_TRY(cudaMemset2DAsync(w.AL, ldL * sizeof(float), 0, L * sizeof(float), L, s));
+    ap_result r;
+    const int32_t st = ap_iterate(w.SL, w.RL, w.AL, L, ldL, params, nullptr, &r, w.sub_ws, w.sub_bytes, s);
+    if (st < 0) return st;
+    const int32_t se = exemplars_impl(w.SL, w.RL, w.AL, L, ldL, w.idxL, &r, w.sub_ws, w.sub_bytes, s);
+    if (se < 0) return se;
+    return se == AP_NO_EXEMPLARS ? 0 : 1;
+}
+
+}  // namespace apgb
+
+APGB_API size_t lap_run_full_workspace_size(int64_t n, int64_t d, int64_t n_landmarks, int64_t m0,
+                                            int32_t max_levels) {
+    if (n < 2 || d < 1 || n_landmarks < 2 || n_landmarks > n || m0 < 2 || m0 > n ||
+        max_levels < 1 || max_levels > AP_LAP_MAX_LEVELS || n > INT_MAX / 2 || d > 65536)
+        return 0;
+    LapFullWs w;
+    return carve_lap_full(nullptr, n, d, n_landmarks, m0, max_levels, &w);
+}
+
+APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t L,
+                              int64_t m0, uint64_t seed, int32_t precision, const ap_params* params,
+                              int32_t max_levels, int32_t* idx, int32_t* level_of,
+                              lap_full_result* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !idx || !out || !params || ldx < d ||
+        !lap_run_full_workspace_size(n, d, L, m0, max_levels))
+        return AP_ERR_INVALID_ARG;
+    if (precision != AP_PREC_FP32 && precision != AP_PREC_BF16) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LapFullWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_lap_full(nullptr, n, d, L, m0, max_levels, &w)));
+    carve_lap_full(ws, n, d, L, m0, max_levels, &w);
+    const int di = (int)d;
+    const int dpad = (di + 63) / 64 * 64;
+    cudaEvent_t ev[2];
+    for (auto& e : ev) AP_CUDA_TRY(cudaEventCreate(&e));
+    struct Guard {
+        cudaEvent_t* e;
+        ~Guard() { for (int i = 0; i < 2; ++i) cudaEventDestroy(e[i]); }
+    } guard{ev};
+    AP_CUDA_TRY(cudaEventRecord(ev[0], s));
+    *out = lap_full_result{};
+    if (level_of) fill_i32_kernel<<<grid_for(n), 256, 0, s>>>(level_of, n, -1);
+    AP_CUDA_TRY(cudaMemsetAsync(w.lap.err, 0, sizeof(int32_t), s));
+    note_launches(1);
+
+    const float* Xl = X;
+    int64_t ldl = ldx, nl = n;
+    const int32_t* ids = nullptr;          // level 0: the identity
+    int cur = 1;
+    int64_t nE = 0;
+    float p = 0.f;
+    bool have_p = false;
+    for (int level = 0;; ++level) {
+        if (level > 0 && nl <= m0) {
+            // ---- Step 3: Algorithm 1 on the points left ----
+            out->base_case = 1;
+            int32_t added = 0;
+            if (nl == 1) {
+                AP_CUDA_TRY(cudaMemcpyAsync(w.E + nE, ids, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                added = 1;
+            } else {
+                const int64_t ldm = ld32(nl);
+                AP_TRY(ap_similarity(Xl, nl, d, ldl, w.Sm, ldm, precision, AP_PREF_SCALAR, &p, 0.0, 0,
+                                     nullptr, w.sub, w.sub_bytes, s));
+                AP_CUDA_TRY(cudaMemset2DAsync(w.Rm, ldm * sizeof(float), 0, nl * sizeof(float), nl, s));
+                AP_CUDA_TRY(cudaMemset2DAsync(w.Am, ldm * sizeof(float), 0, nl * sizeof(float), nl, s));
+                ap_result r;
+                const int32_t st = ap_iterate(w.Sm, w.Rm, w.Am, nl, ldm, params, nullptr, &r, w.sub,
+                                              w.sub_bytes, s);
+                if (st < 0) return st;
+                const int32_t se = exemplars_impl(w.Sm, w.Rm, w.Am, nl, ldm, w.idxm, &r, w.sub,
+                                                  w.sub_bytes, s);
+                if (se < 0) return se;
+                if (se != AP_NO_EXEMPLARS) {
+                    landmark_exemplars_kernel<<<1, 1024, 0, s>>>(w.idxm, nl, ids, w.E + nE, w.cnt);
+                    AP_CUDA_TRY(cudaMemcpyAsync(&added, w.cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+                    AP_CUDA_TRY(cudaStreamSynchronize(s));
+                    note_launches(1);
+                }
+            }
+            if (level_of) {                 // every point of Step 3 is settled at this level
+                set_level_kernel<<<grid_for(nl), 256, 0, s>>>(ids, nl, level, level_of);
+                note_launches(1);
+            }
+            if (nE + added > w.emax) return AP_ERR_TOO_LARGE;
+            nE += added;
+            out->exemplars_at[level] = added;
+            break;
+        }
+        // ---- Step 1: landmarks of this level and Algorithm 1 on them ----
+        const int64_t Ll = std::min(L, nl);
+        keys_uniform_kernel<<<grid_for(nl), 256, 0, s>>>(seed + (uint64_t)level, nl, w.lap.keys);
+        note_launches(1);
+        AP_TRY(select_smallest(w.lap.keys, nl, Ll, w.lap.ks, w.lap.hist, w.lap.lm, s));
+        gather_rows_kernel<<<(int)std::min<int64_t>(Ll, 65535), 128, 0, s>>>(Xl, ldl, di, w.lap.lm, Ll,
+                                                                              w.lap.XL);
+        note_launches(1);
+        const int32_t got = landmark_ap(w.lap, Ll, d, precision, params, have_p, &p, s);
+        if (got < 0) return got;
+        have_p = true;
+        if (got == 0) {
+            if (level == 0) {
+                AP_CUDA_TRY(cudaMemsetAsync(idx, 0xFF, sizeof(int32_t) * n, s));
+                AP_CUDA_TRY(cudaStreamSynchronize(s));
+                out->pref = p;
+                out->dpsim = out->expref = out->netsim = NAN;
+                return AP_NO_EXEMPLARS;
+            }
+            break;                          // the points left join their nearest exemplar in Step 4
+        }
+        out->levels = level + 1;
+        // ---- Step 2: max_distance per class, nearest exemplar, the gate ----
+        landmark_exemplars_kernel<<<1, 1024, 0, s>>>(w.lap.idxL, Ll, w.lap.lm, w.lap.epts, w.lap.ecount);
+        exemplar_slots_kernel<<<1, 1024, 0, s>>>(w.lap.idxL, Ll, w.slot);
+        int32_t c = 0;
+        AP_CUDA_TRY(cudaMemcpyAsync(&c, w.lap.ecount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaStreamSynchronize(s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.maxd, 0, sizeof(unsigned) * c, s));
+        max_distance_kernel<<<(int)((Ll + 255) / 256), 256, 0, s>>>(w.lap.SL, ld32(Ll), w.lap.idxL, w.slot,
+                                                                     Ll, w.maxd);
+        const int nb = (int)((nl + 4095) / 4096);
+        colsum_rows_kernel<<<nb, 128, 0, s>>>(Xl, nl, di, ldl, 4096, w.lap.part);
+        colmean_rows_kernel<<<(di + 127) / 128, 128, 0, s>>>(w.lap.part, nb, di, nl, w.lap.mean);
+        const int64_t npad = (nl + 127) / 128 * 128, cpad = ((int64_t)c + 255) / 256 * 256;
+        centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
+            Xl, ldl, di, nullptr, nl, npad, dpad, w.lap.mean, w.lap.Xb, w.xnrm);
+        centre_bf16_kernel<<<(int)std::min<int64_t>((cpad + 7) / 8, 65535), 256, 0, s>>>(
+            Xl, ldl, di, w.lap.epts, c, cpad, dpad, w.lap.mean, w.lap.Eb, w.lap.enrm);
+        note_launches(7);
+        AP_TRY(last_error());
+        AP_TRY(tc_assign_argmax(w.lap.Xb, (int)nl, w.lap.Eb, c, w.lap.enrm, dpad, w.lap.arg, w.best,
+                                w.lap.err, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.is_lm, 0, sizeof(int32_t) * nl, s));
+        flag_rows_kernel<<<grid_for(Ll), 256, 0, s>>>(w.lap.lm, Ll, w.is_lm);
+        gate_kernel<<<grid_for(nl), 256, 0, s>>>(nl, w.lap.arg, w.best, w.xnrm, w.maxd, w.is_lm, ids,
+                                                 level, w.un, level_of);
+        if (nE + c > w.emax) return AP_ERR_TOO_LARGE;
+        map_ids_kernel<<<grid_for(c), 256, 0, s>>>(w.lap.epts, c, ids, w.E + nE, level, level_of);
+        nE += c;
+        out->exemplars_at[level] = c;
+        compact_flags_kernel<<<1, 1024, 0, s>>>(w.un, nl, w.list, w.cnt);
+        note_launches(5);
+        AP_TRY(last_error());
+        int32_t m = 0;
+        AP_CUDA_TRY(cudaMemcpyAsync(&m, w.cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaStreamSynchronize(s));
+        out->unassigned[level] = m;
+        if (m == 0 || level + 1 >= max_levels) break;
+        // ---- Step 3 (recursive case): the points left become the next level ----
+        const int nxt = cur ^ 1;
+        gather_rows_kernel<<<(int)std::min<int64_t>(m, 65535), 128, 0, s>>>(Xl, ldl, di, w.list, m,
+                                                                             w.Xn[nxt]);
+        map_ids_kernel<<<grid_for(m), 256, 0, s>>>(w.list, m, ids, w.ids[nxt], 0, nullptr);
+        note_launches(2);
+        Xl = w.Xn[nxt];
+        ldl = d;
+        ids = w.ids[nxt];
+        nl = m;
+        cur = nxt;
+    }
+
+    // ---- Step 4: every point to its nearest exemplar of the merged set ----
+    std::vector<int32_t> hE(nE);
+    AP_CUDA_TRY(cudaMemcpyAsync(hE.data(), w.E, sizeof(int32_t) * nE, cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    std::sort(hE.begin(), hE.end());
+    AP_CUDA_TRY(cudaMemcpyAsync(w.E, hE.data(), sizeof(int32_t) * nE, cudaMemcpyHostToDevice, s));
+    const int nb = (int)((n + 4095) / 4096);
+    colsum_rows_kernel<<<nb, 128, 0, s>>>(X, n, di, ldx, 4096, w.lap.part);
+    colmean_rows_kernel<<<(di + 127) / 128, 128, 0, s>>>(w.lap.part, nb, di, n, w.lap.mean);
+    const int64_t npad = (n + 127) / 128 * 128, epad = (nE + 255) / 256 * 256;
+    centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, nullptr, n, npad, dpad, w.lap.mean, w.lap.Xb, nullptr);
+    centre_bf16_kernel<<<(int)std::min<int64_t>((epad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, w.E, nE, epad, dpad, w.lap.mean, w.Eb, w.enrm);
+    note_launches(4);
+    AP_TRY(last_error());
+    AP_TRY(tc_assign_argmax(w.lap.Xb, (int)n, w.Eb, (int)nE, w.enrm, dpad, w.lap.arg, nullptr,
+                            w.lap.err, s));
+    labels_kernel<<<grid_for(n), 256, 0, s>>>(w.lap.arg, n, w.E, idx);
+    exemplars_keep_self_kernel<<<(int)((nE + 255) / 256), 256, 0, s>>>(w.E, (int)nE, idx);
+    lap_dpsim_kernel<<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, s>>>(X, ldx, di, n, idx,
+                                                                                   w.lap.dp);
+    sum_f64_kernel<<<1, 1024, 0, s>>>(w.lap.dp, n, w.lap.sums);
+    note_launches(4);
+    AP_TRY(last_error());
+    AP_CUDA_TRY(cudaEventRecord(ev[1], s));
+    double dps = 0.0;
+    int32_t err = 0;
+    AP_CUDA_TRY(cudaMemcpyAsync(&dps, w.lap.sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.lap.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return AP_ERR_TIMEOUT;
+    AP_CUDA_TRY(cudaEventElapsedTime(&out->ms, ev[0], ev[1]));
+    out->pref = p;
+    out->n_exemplars = (int32_t)nE;
+    out->dpsim = dps;
+    out->expref = (double)p * (double)nE;
+    out->netsim = out->dpsim + out->expref;
+    return AP_OK;
 }

@@ -109,3 +109,63 @@ def test_lap_given_landmarks_and_bf16_landmark_similarity():
     E = np.unique(labels)
     assert set(E) <= set(lm_in.tolist())
     _check_assignment(X, E, labels)
+
+
+# ---- Algorithm 3 Steps 1-4 -------------------------------------------------------------
+
+def _far_data(seed):
+    """A 10-Gaussian mixture in R^8 plus a tight group of 10 points far from
+    it (indices 2990-2999), which no landmark class can hold."""
+    X, _ = synth.gaussian_mixture(2990, 8, 10, 900 + seed, 6.0, 1.0)
+    g = np.random.default_rng(seed)
+    far = 60.0 + 0.2 * g.normal(size=(10, 8))
+    return np.vstack([X, far]).astype(np.float32)
+
+
+@pytest.mark.parametrize("dseed", [1, 2])
+def test_lap_full_matches_oracle(dseed):
+    """Steps 1-4 against the oracle on data whose gate and nearest-exemplar
+    decisions are all clear of float32 rounding (asserted on the oracle's
+    margins), so both sides must take every decision the same way.  Damping
+    0.9: at 0.5 the landmark problem of this mixture is ill-conditioned (the
+    float32 and float64 runs stop at different exemplar sets)."""
+    X = _far_data(dseed)
+    L, m0, seed = 300, 1000, 1
+    assert not np.isin(np.arange(2990, 3000), olap.uniform_landmarks(X.shape[0], L, seed)).any()
+    ref = olap.run_full(X, L, seed, m0, lam=0.9, max_iter=1000, convits=15)
+    l0 = ref["levels"][0]
+    assert (l0["margin"] / l0["scale"]).min() > 1e-4 and (l0["gap"] / l0["scale"]).min() > 1e-4
+    assert (ref["gap"] / l0["scale"]).min() > 1e-4
+    idx, level_of, res = capi.lap_run_full(torch.from_numpy(X).cuda(), L, m0, seed=seed,
+                                           precision="fp32", damping=0.9, max_iter=1000,
+                                           conv_iter=15)
+    idx = idx.cpu().numpy().astype(np.int64)
+    level_of = level_of.cpu().numpy()
+    assert res["levels"] == 1 and res["base_case"] == 1 and len(ref["levels"]) == 2
+    assert res["unassigned"][0] == l0["unassigned"].size
+    assert np.array_equal(np.nonzero(level_of != 0)[0], l0["unassigned"])
+    assert np.all(level_of[l0["unassigned"]] == 1)
+    assert res["exemplars_at"] == [l0["E"].size, ref["levels"][1]["E"].size]
+    assert np.array_equal(np.unique(idx), ref["E"]) and res["n_exemplars"] == ref["E"].size
+    assert np.array_equal(idx, ref["idx"])
+    assert np.all(idx[2990:] >= 2990)                 # the far group has its own exemplar
+    assert abs(res["netsim"] - ref["netsim"]) <= 1e-5 * abs(ref["netsim"])
+
+
+def test_lap_full_recursion_and_invariants():
+    """m0 below the points left: Step 3 recurses (more landmark levels), the
+    merged set labels every point, exemplars label themselves, labels are the
+    nearest exemplar (checked in the assignment's precision)."""
+    X = _far_data(1)
+    idx, level_of, res = capi.lap_run_full(torch.from_numpy(X).cuda(), 100, 20, seed=4,
+                                           precision="bf16", damping=0.5, max_iter=1000,
+                                           conv_iter=15)
+    idx = idx.cpu().numpy().astype(np.int64)
+    level_of = level_of.cpu().numpy()
+    assert res["levels"] >= 2
+    E = np.unique(idx)
+    assert E.size == res["n_exemplars"] == sum(res["exemplars_at"])
+    assert np.all(idx[E] == E)
+    assert np.all(idx[2990:] >= 2990)
+    assert level_of.min() >= -1 and level_of.max() <= res["levels"]
+    _check_assignment(X, E, idx)

@@ -10,6 +10,7 @@ import pytest
 from scipy.spatial.distance import cdist
 
 from oracle import ap, lap, pap, rng
+from paper_0910_1650_gb300 import synth
 
 
 def _load(golden_dir, name):
@@ -493,3 +494,71 @@ def test_round_bf16_vs_torch():
 def test_centring_preserves_distances():
     X = np.random.default_rng(4).normal(size=(40, 5)).astype(np.float32) + 100
     assert np.allclose(ap.similarity(ap.centred(X)), ap.similarity(X), rtol=1e-5, atol=1e-3)
+
+
+# ---- Algorithm 3 Steps 1-4 (oracle.lap.run_full) ----------------------------------------
+
+def _far_group_data(seed=0):
+    g = np.random.default_rng(seed)
+    A = g.normal(size=(200, 2))
+    far = np.array([1000.0, 1000.0]) + 0.1 * g.normal(size=(5, 2))
+    return np.vstack([A, far]).astype(np.float32)
+
+
+def test_lap_full_every_point_a_landmark_is_ap():
+    """L = n: Step 1 is Algorithm 1 on all points, the gate keeps every point
+    (all are landmarks), Step 4 is the nearest-exemplar assignment, which at
+    convergence is AP's own assignment."""
+    X = synth.gaussian_mixture(120, 2, 4, 5, 8.0, 1.0)[0]
+    full = lap.run_full(X, 120, seed=3, m0=50, lam=0.9, max_iter=1000, convits=15)
+    S, p = ap.build_similarity(X)
+    res = ap.run(S, 0.9, 1000, 15)
+    ex = ap.exemplars(S, res["R"], res["A"])
+    assert full["levels"][0]["unassigned"].size == 0 and len(full["levels"]) == 1
+    assert np.array_equal(full["E"], ex["E"])
+    assert np.array_equal(full["idx"], ex["idx"])
+
+
+def test_lap_full_one_level_equals_steps_1_2_on_separated_data():
+    X = synth.gaussian_mixture(600, 3, 6, 9, 20.0, 0.5, False)[0]
+    lm = lap.uniform_landmarks(600, 150, 21)
+    a = lap.run(X, lm, lam=0.9, max_iter=1000, convits=15)
+    b = lap.run_full(X, 150, seed=21, m0=600, lam=0.9, max_iter=1000, convits=15, max_levels=1)
+    assert np.array_equal(a["E"], b["E"])
+    assert np.array_equal(a["idx"], b["idx"])
+    assert abs(a["netsim"] - b["netsim"]) <= 1e-9 * abs(a["netsim"])
+
+
+def test_lap_full_gate_gives_unreached_points_their_own_exemplar():
+    """A tight group far from every landmark class fails Step 2's gate; Step 3
+    (Algorithm 1 on the points left) makes an exemplar among them, where
+    Steps 1-2 alone would have labelled them with a far-away exemplar."""
+    X = _far_group_data()
+    n = X.shape[0]
+    seed = next(s for s in range(100)
+                if not np.isin(np.arange(200, 205), lap.uniform_landmarks(n, 40, s)).any())
+    # damping 0.5 (the paper's): at 0.9 the stop rule can fire on the points
+    # left before their messages have grown (decisions constant from t = 1)
+    full = lap.run_full(X, 40, seed=seed, m0=100, lam=0.5, max_iter=1000, convits=15)
+    un0 = full["levels"][0]["unassigned"]
+    assert set(range(200, 205)) <= set(un0.tolist())
+    far_labels = full["idx"][200:205]
+    assert np.all(far_labels >= 200)                  # an exemplar of the far group
+    plain = lap.run(X, lap.uniform_landmarks(n, 40, seed), lam=0.5, max_iter=1000, convits=15)
+    assert np.all(plain["idx"][200:205] < 200)        # Steps 1-2 alone: a far-away exemplar
+    assert full["netsim"] > plain["netsim"]
+
+
+def test_lap_full_recursion_when_m_exceeds_m0():
+    """m0 below the number of points left forces Step 3's recursive branch:
+    a second level of Steps 1-2 on the points left."""
+    X = _far_group_data(1)
+    n = X.shape[0]
+    seed = next(s for s in range(100)
+                if not np.isin(np.arange(200, 205), lap.uniform_landmarks(n, 40, s)).any())
+    full = lap.run_full(X, 40, seed=seed, m0=2, lam=0.5, max_iter=1000, convits=15)
+    assert len(full["levels"]) >= 2 and full["levels"][0]["unassigned"].size > 2
+    assert np.all(full["idx"][200:205] >= 200)
+    # every label is an exemplar of the merged set, and exemplars label themselves
+    assert set(np.unique(full["idx"]).tolist()) == set(full["E"].tolist())
+    assert np.all(full["idx"][full["E"]] == full["E"])
