@@ -391,9 +391,10 @@ def time_to_converge(dev):
     out = {}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
-    def timed(fn):
-        fn()                        # untimed first run: allocator misses stay outside
-        torch.cuda.synchronize()
+    def timed(fn, warm=True):
+        if warm:
+            fn()                    # untimed first run: allocator misses stay outside
+            torch.cuda.synchronize()
         ev[0].record()
         r = fn()
         ev[1].record()
@@ -432,6 +433,23 @@ def time_to_converge(dev):
         "time_ratio_plain_over_pap": round(t_plain / t_pap, 3),
         "netsim_rel_diff": (pr["final"]["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
     }
+    # the same 32 uneven subsets with Step 4 also starting from the subsets' R,
+    # and the paper's equal partition at several k (Table 2's k-sensitivity)
+    (_, _, _, pc), t_pc = timed(lambda: capi.pap_run(S, len(offs) - 1, list(offs), damping=DAMPING,
+                                                     max_iter=MAX_ITER, conv_iter=CONV_ITER,
+                                                     R=R, A=A, carry_r=True), warm=False)
+    out["pap"]["carry_r"] = {"ms": round(t_pc, 1), "step4_iters": pc["final"]["iters"],
+                             "netsim_rel_diff": (pc["final"]["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
+                             "time_ratio_plain_over_pap": round(t_plain / t_pc, 3)}
+    sweep = []
+    for k in (8, 16, 32, 64):
+        (_, _, _, pk), t_k = timed(lambda: capi.pap_run(S, k, None, damping=DAMPING, max_iter=MAX_ITER,
+                                                        conv_iter=CONV_ITER, R=R, A=A), warm=False)
+        sweep.append({"k": k, "ms": round(t_k, 1), "sub_iters_max": pk["sub_iters_max"],
+                      "step4_iters": pk["final"]["iters"],
+                      "netsim_rel_diff": (pk["final"]["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
+                      "time_ratio_plain_over_pap": round(t_plain / t_k, 3)})
+    out["pap"]["k_sweep_equal_partition"] = sweep
     del S, R, A
     torch.cuda.empty_cache()
 

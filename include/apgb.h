@@ -80,6 +80,10 @@ typedef struct ap_params {
  * workspace address and launch shape are seen, kept (up to 32 per process),
  * and launched on the caller's stream. */
 #define AP_FLAG_NO_GRAPH   2
+/* ap_params.flags, pap_run only: Step 4 starts from the block-diagonal R of
+ * the sub-problems as well as A' (the paper carries availabilities only, so
+ * R = 0 without this flag). */
+#define AP_FLAG_PAP_CARRY_R 4
 
 /* Outputs of Algorithm 1 (Section 2): dpsim = sum of the data-point
  * similarities to their exemplars, expref = sum of the exemplars'

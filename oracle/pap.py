@@ -40,9 +40,11 @@ def merge_blocks(n: int, offsets, blocks) -> np.ndarray:
     return Ap
 
 
-def run(S, offsets, lam=0.5, max_iter=200, convits=15, fixed_iters=None):
+def run(S, offsets, lam=0.5, max_iter=200, convits=15, fixed_iters=None, carry_r=False):
     """Algorithm 2 with the given block offsets.  With ``fixed_iters`` every
-    run (Step 2 and Step 4) takes exactly that many iterations.
+    run (Step 2 and Step 4) takes exactly that many iterations.  Step 4
+    starts from R = 0 (the paper carries availabilities only) or, with
+    ``carry_r`` (a variant), from the block-diagonal R of the sub-problems.
 
     Returns dict(sub=[per-block run dicts], A_prime, final=run dict of Step 4)."""
     S = np.asarray(S, dtype=np.float64)
@@ -52,5 +54,6 @@ def run(S, offsets, lam=0.5, max_iter=200, convits=15, fixed_iters=None):
         lo, hi = int(offsets[j]), int(offsets[j + 1])
         subs.append(ap.run(S[lo:hi, lo:hi], lam, max_iter, convits, fixed_iters=fixed_iters))
     Ap = merge_blocks(n, offsets, [s["A"] for s in subs])
-    final = ap.run(S, lam, max_iter, convits, R0=np.zeros((n, n)), A0=Ap, fixed_iters=fixed_iters)
+    R0 = merge_blocks(n, offsets, [s["R"] for s in subs]) if carry_r else np.zeros((n, n))
+    final = ap.run(S, lam, max_iter, convits, R0=R0, A0=Ap, fixed_iters=fixed_iters)
     return dict(sub=subs, A_prime=Ap, final=final)

@@ -24,6 +24,7 @@ AP_PREC_FP32, AP_PREC_BF16 = 0, 1
 AP_PREF_MEDIAN, AP_PREF_SCALAR, AP_PREF_VECTOR = 0, 1, 2
 AP_FLAG_TIME_SWEEP = 1
 AP_FLAG_NO_GRAPH = 2
+AP_FLAG_PAP_CARRY_R = 4
 AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
 AP_NOALLOC_MAX_N = 65536
@@ -377,7 +378,7 @@ def ap_iterate_batched(S, R, A, offsets, n, ld, damping=0.5, max_iter=200, conv_
 
 
 def pap_run(S, k, part_offsets=None, damping=0.5, max_iter=200, conv_iter=15, check_every=0,
-            R=None, A=None, stream=None):
+            R=None, A=None, carry_r=False, stream=None):
     """Algorithm 2 on S (n x n).  Returns (R, A, idx, result dict)."""
     _dev_f32(S, "S")
     n = S.shape[0]
@@ -386,7 +387,8 @@ def pap_run(S, k, part_offsets=None, damping=0.5, max_iter=200, conv_iter=15, ch
     idx = torch.empty(n, dtype=torch.int32, device=S.device)
     part = _i64_array(part_offsets) if part_offsets is not None else None
     partp = C.cast(part, C.c_void_p) if part is not None else None
-    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every),
+                 AP_FLAG_PAP_CARRY_R if carry_r else 0)
     res = PapResult()
     ws = workspace(lib().pap_run_workspace_size(n, S.stride(0), int(k), partp), S.device)
     st = lib().pap_run(C.c_void_p(S.data_ptr()), n, S.stride(0), int(k), partp, C.byref(p),

@@ -171,11 +171,15 @@ APGB_API int32_t pap_run(const float* S, int64_t n, int64_t ld, int32_t k, const
     if (st_sub < 0) return st_sub;
     AP_CUDA_TRY(cudaEventRecord(ev[1], s));
 
-    // Step 3: A' = blockdiag(A_jj), R = 0
+    // Step 3: A' = blockdiag(A_jj), R = 0 (or R' = blockdiag(R_jj) with AP_FLAG_PAP_CARRY_R)
     AP_CUDA_TRY(cudaMemset2DAsync(A, ld * sizeof(float), 0, n * sizeof(float), n, s));
     AP_CUDA_TRY(cudaMemset2DAsync(R, ld * sizeof(float), 0, n * sizeof(float), n, s));
     scatter_blocks_kernel<<<grid, 256, 0, s>>>(w.Aa, w.blocks, A, ld);
     note_launches(1);
+    if (params->flags & AP_FLAG_PAP_CARRY_R) {
+        scatter_blocks_kernel<<<grid, 256, 0, s>>>(w.Ra, w.blocks, R, ld);
+        note_launches(1);
+    }
     AP_TRY(last_error());
     AP_CUDA_TRY(cudaEventRecord(ev[2], s));
 

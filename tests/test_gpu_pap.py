@@ -108,6 +108,23 @@ def test_pap_fixed_iterations_matches_oracle(k, part):
     assert rel_inf(A.cpu().numpy().astype(np.float64), ref["final"]["A"]) <= TOL
 
 
+@pytest.mark.parametrize("k,part", [(4, None), (3, [0, 150, 420, 600])])
+def test_pap_carry_r_matches_oracle(k, part):
+    """The variant that starts Step 4 from the block-diagonal R as well as A'."""
+    S = _pap_case()
+    n = S.shape[0]
+    Sd = capi.empty_square(n, "cuda")
+    Sd.copy_(torch.from_numpy(S.astype(np.float32)).cuda())
+    R, A, idx, res = capi.pap_run(Sd, k, part, damping=0.9, max_iter=15, conv_iter=0, carry_r=True)
+    offs = part if part is not None else opap.equal_partition(n, k)
+    ref = opap.run(S, offs, lam=0.9, fixed_iters=15, carry_r=True)
+    assert rel_inf(R.cpu().numpy().astype(np.float64), ref["final"]["R"]) <= TOL
+    assert rel_inf(A.cpu().numpy().astype(np.float64), ref["final"]["A"]) <= TOL
+    # and it differs from the paper's form, which starts Step 4 from R = 0
+    R0, _, _, _ = capi.pap_run(Sd, k, part, damping=0.9, max_iter=15, conv_iter=0)
+    assert not torch.equal(R0, R)
+
+
 def test_pap_converged_matches_oracle_and_plain_ap():
     S = _pap_case(1200)
     n = S.shape[0]

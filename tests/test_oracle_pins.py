@@ -562,3 +562,20 @@ def test_lap_full_recursion_when_m_exceeds_m0():
     # every label is an exemplar of the merged set, and exemplars label themselves
     assert set(np.unique(full["idx"]).tolist()) == set(full["E"].tolist())
     assert np.all(full["idx"][full["E"]] == full["E"])
+
+
+def test_pap_carry_r_single_block_continues_the_run():
+    """With one block, carrying R and A into Step 4 continues the same run:
+    t sub-iterations then t Step-4 iterations equal 2t plain iterations
+    (the iteration is a map of (R, A) alone)."""
+    g = np.random.default_rng(12)
+    S, _ = ap.build_similarity(g.normal(size=(40, 3)))
+    n = S.shape[0]
+    t = 9
+    two = pap.run(S, [0, n], lam=0.7, fixed_iters=t, carry_r=True)
+    straight = ap.run(S, 0.7, fixed_iters=2 * t)
+    assert np.allclose(two["final"]["R"], straight["R"], rtol=0, atol=1e-12 * np.abs(S).max())
+    assert np.allclose(two["final"]["A"], straight["A"], rtol=0, atol=1e-12 * np.abs(S).max())
+    # without carrying R the paper's Step 4 restarts R from 0 and does not continue the run
+    one = pap.run(S, [0, n], lam=0.7, fixed_iters=t)
+    assert not np.allclose(one["final"]["R"], straight["R"], rtol=0, atol=1e-6 * np.abs(S).max())
