@@ -286,6 +286,7 @@ def run_gpu(args):
             line["time_to_converge"] = time_to_converge(dev)
             line["small_problem"] = small_problem(dev)
             line["batch_learned"] = batch_learned(dev)
+            line["paper_2d"] = paper_2d(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -326,6 +327,83 @@ def small_problem(dev, reps=20):
         out[key] = {"iters": r["iters"], "ms_to_converge": round(ms, 4),
                     "us_per_iter": round(ms * 1e3 / max(r["iters"], 1), 3)}
     return out
+
+
+def _agreement(ref, got):
+    """Fraction of points whose cluster under ``got``, mapped to the ``ref``
+    cluster holding most of its points, equals their ``ref`` cluster (the
+    reading of Table 1's undefined "accuracy")."""
+    ref = np.asarray(ref)
+    got = np.asarray(got)
+    ok = 0
+    for g in np.unique(got):
+        members = ref[got == g]
+        ok += np.bincount(np.unique(members, return_inverse=True)[1]).max()
+    return ok / ref.size
+
+
+def paper_2d(dev, reps=10):
+    """The paper's 2-D experiments on seeded stand-ins (5-Gaussian 2-D
+    mixtures, damping 0.5): AP against partition AP with k = 4 at N = 100,
+    1000, 2000, 3000 (Fig. 2), and AP against landmark AP with 100-500
+    landmarks at N = 1000 (Table 1), each averaged over ``reps`` seeded sets.
+    Device time of whole calls (CUDA events)."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ev[0].record()
+        r = fn()
+        ev[1].record()
+        ev[1].synchronize()
+        return r, ev[0].elapsed_time(ev[1])
+
+    kw = dict(damping=0.5, max_iter=1000, conv_iter=15)
+    fig2 = []
+    for n in (100, 1000, 2000, 3000):
+        it_ap, ms_ap, it_pap, ms_pap, rel = [], [], [], [], []
+        for r in range(reps):
+            X, _ = synth.gaussian_mixture_2d(seed=synth.SEED_BASE + 500 + 10 * n + r,
+                                             per_cluster=n // 5)
+            S, _ = capi.ap_similarity(torch.from_numpy(X).to(dev), precision="fp32")
+            (R, A, ra, _), t = timed(lambda: capi.ap_iterate(S, **kw))
+            _, ea = capi.ap_exemplars(S, R, A)
+            (_, _, _, rp), tp = timed(lambda: capi.pap_run(S, 4, None, **kw))
+            it_ap.append(ra["iters"]); ms_ap.append(t)
+            it_pap.append(rp["final"]["iters"]); ms_pap.append(tp)
+            rel.append((rp["final"]["netsim"] - ea["netsim"]) / abs(ea["netsim"]))
+        fig2.append({"n": n, "ap_iters": round(float(np.mean(it_ap)), 1), "ap_ms": round(float(np.mean(ms_ap)), 2),
+                     "pap_step4_iters": round(float(np.mean(it_pap)), 1),
+                     "pap_ms": round(float(np.mean(ms_pap)), 2),
+                     "netsim_rel_diff_mean": float(np.mean(rel))})
+    table1 = []
+    base = []
+    for r in range(reps):
+        X, _ = synth.gaussian_mixture_2d(seed=synth.SEED_BASE + 600 + r, per_cluster=200)
+        Xd = torch.from_numpy(X).to(dev)
+        S, _ = capi.ap_similarity(Xd, precision="fp32")
+        (R, A, _, _), t = timed(lambda: capi.ap_iterate(S, **kw))
+        idx, _ = capi.ap_exemplars(S, R, A)
+        base.append((Xd, idx.cpu().numpy(), t))
+    for L in (500, 400, 300, 200, 100):
+        ms, acc = [], []
+        for r, (Xd, ref, _) in enumerate(base):
+            (idx, _, _), t = timed(lambda: capi.lap_run(Xd, L, "uniform", seed=synth.SEED_BASE + 700 + r,
+                                                        precision="fp32", **kw))
+            ms.append(t)
+            acc.append(_agreement(ref, idx.cpu().numpy()))
+        table1.append({"landmarks": L, "ms": round(float(np.mean(ms)), 2),
+                       "agreement_with_ap": round(float(np.mean(acc)), 4)})
+    return {"workload": "5-Gaussian 2-D mixtures (centres U[-10,10]^2, sigma 1), damping 0.5, max 1000, "
+                        "15 unchanged sweeps; %d seeded sets per point" % reps,
+            "fig2_ap_vs_pap_k4": fig2,
+            "table1": {"n": 1000, "ap_ms": round(float(np.mean([b[2] for b in base])), 2),
+                       "lap": table1,
+                       "agreement": "fraction of points whose LAP cluster, mapped to its majority AP "
+                                    "cluster, is their AP cluster"}}
 
 
 def batch_learned(dev, count=256, n_train=32):
@@ -611,6 +689,25 @@ def similarity_only(args):
                       "ms": round(ms, 4), "tflops": round(fl / ms / 1e9, 1)}), flush=True)
 
 
+def lap_only(args):
+    """Landmark AP alone (Steps 1-2 of Algorithm 3: landmark similarity and
+    AP, then the tensor-core nearest-exemplar assignment) on the first N
+    points of the 1e6-point workload, for profiling the assignment GEMM."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    X, _ = synth.workload(3, scale=args.lap_only / 1_000_000)
+    Xd = torch.from_numpy(X).cuda()
+    _, _, r = capi.lap_run(Xd, min(20000, args.lap_only), "uniform", seed=synth.config_seed(3),
+                           precision="bf16", damping=DAMPING, max_iter=MAX_ITER, conv_iter=CONV_ITER)
+    c = r["n_exemplars"]
+    fl = 2.0 * args.lap_only * c * X.shape[1]
+    print(json.dumps({"case": "lap", "n": args.lap_only, "exemplars": c, "assign_ms": round(r["assign_ms"], 3),
+                      "assign_tflops": round(fl / r["assign_ms"] / 1e9, 1), "ms": round(r["landmark_ms"], 2)}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,12 +722,18 @@ def main():
                     help="skip the time-to-converge comparisons (partition and landmark AP)")
     ap.add_argument("--n", type=int, default=N_POINTS,
                     help="points (default: the 20000-point workload; smaller for profiling)")
+    ap.add_argument("--lap-only", type=int, default=0, metavar="N",
+                    help="profiling aid: one landmark AP (Steps 1-2, 20000 landmarks, bf16) on the "
+                         "first N points of the 1e6-point workload, print one JSON line")
     ap.add_argument("--similarity-only", type=int, default=0, metavar="D",
                     help="profiling aid: time the bf16 similarity build alone on one image-like "
                          "problem of --n points and D features, print one JSON line")
     args = ap.parse_args()
     if args.similarity_only:
         similarity_only(args)
+        return
+    if args.lap_only:
+        lap_only(args)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

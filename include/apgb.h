@@ -481,6 +481,12 @@ int32_t   ap_exemplars_noalloc(const float* S, const float* R, const float* A,
 /* ---- misc ------------------------------------------------------------------ */
 const char* ap_status_string(int32_t status);
 int32_t     ap_version(void);            /* major*10000 + minor*100 + patch   */
+/* Failure-detection self-test (no counterpart in the paper): one CTA waits on
+ * an mbarrier that nothing completes, with the bounded try-wait loop every
+ * device wait of the library uses (spin_limit tries).  Returns
+ * AP_ERR_TIMEOUT when the bound runs out, as it always should; the context
+ * stays usable.  Synchronises ``stream``. */
+int32_t     ap_wait_selftest(uint32_t spin_limit, void* stream);
 /* Number of kernels this library has launched in this process (all devices,
  * all threads); for accounting in benchmarks. */
 uint64_t    ap_kernel_launches(void);

@@ -27,6 +27,7 @@ AP_FLAG_NO_GRAPH = 2
 AP_FLAG_PAP_CARRY_R = 4
 AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
+AP_ERR_TIMEOUT = -4
 AP_NOALLOC_MAX_N = 65536
 
 
@@ -166,6 +167,7 @@ _SIGNATURES = {
     "ap_status_string": (C.c_char_p, [C.c_int32]),
     "ap_version": (C.c_int32, []),
     "ap_kernel_launches": (C.c_uint64, []),
+    "ap_wait_selftest": (C.c_int32, [C.c_uint32, _P]),
 }
 
 
@@ -597,3 +599,8 @@ def apl_ap_run(S, P, P16, scale, damping=0.9, max_iter=1000, conv_iter=15, judge
                           ws.numel(), _stream(stream))
     _check("apl_ap_run", st)
     return R, A, idx, res.as_dict()
+
+
+def ap_wait_selftest(spin_limit=1 << 16, stream=None):
+    """Status of the library's bounded-wait self-test (AP_ERR_TIMEOUT expected)."""
+    return int(lib().ap_wait_selftest(int(spin_limit), _stream(stream)))

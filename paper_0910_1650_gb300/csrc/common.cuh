@@ -63,6 +63,12 @@ inline int32_t last_error() {
 
 int32_t device_sm_count(int* sms);       // cached per device
 void note_launches(uint64_t k);          // feeds ap_kernel_launches()
+// Column means of X (n x d, leading dimension ldx) into mean[d]: compensated
+// float32 partials over row blocks, combined in float64 in a fixed order;
+// part needs column_mean_part_doubles(n, d) doubles.
+size_t column_mean_part_doubles(int64_t n, int d);
+int32_t column_means(const float* X, int64_t n, int d, int64_t ldx, double* part, float* mean,
+                     cudaStream_t s);
 int32_t require_sm103();                 // AP_ERR_UNSUPPORTED on other GPUs
 
 // ---- device helpers ------------------------------------------------------

@@ -149,26 +149,6 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int64_t ldx, int
     }
 }
 
-__global__ void colsum_rows_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ldx,
-                                   int rows_per_block, double* part) {
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r1 = (r0 + rows_per_block < n) ? r0 + rows_per_block : n;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        for (int64_t i = r0; i < r1; ++i) s += (double)X[i * ldx + j];
-        part[(int64_t)blockIdx.x * d + j] = s;
-    }
-}
-
-__global__ void colmean_rows_kernel(const double* __restrict__ part, int nb, int d, int64_t n,
-                                    float* mean) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * d + j];
-    mean[j] = (float)(s / (double)n);
-}
-
 // bf16 of (x - mean) for the listed rows (or rows 0..m-1), zero padded to
 // [mpad x dpad]; optional fp32 squared norms of the rounded rows.
 __global__ void centre_bf16_kernel(const float* __restrict__ X, int64_t ldx, int d,
@@ -421,7 +401,6 @@ static size_t carve_lap(void* ws, int64_t n, int64_t d, int64_t L, LapWs* w) {
                                  exemplars_ws_bytes(L)});
     const int64_t npad = (n + 127) / 128 * 128;
     const int64_t cpad = (L + 255) / 256 * 256;        // at most L exemplars
-    const int nb = (int)((n + 4095) / 4096);
     Carver c(ws);
     w->keys = c.take<uint64_t>(n);
     w->ks = c.take<KSelect>(1);
@@ -436,7 +415,7 @@ static size_t carve_lap(void* ws, int64_t n, int64_t d, int64_t L, LapWs* w) {
     w->sub_bytes = sub;
     w->epts = c.take<int32_t>(L);
     w->ecount = c.take<int32_t>(1);
-    w->part = c.take<double>((size_t)nb * d);
+    w->part = c.take<double>(column_mean_part_doubles(n, (int)d));
     w->mean = c.take<float>(d);
     w->Xb = c.take<__nv_bfloat16>((size_t)npad * dpad);
     w->Eb = c.take<__nv_bfloat16>((size_t)cpad * dpad);
@@ -552,9 +531,7 @@ APGB_API int32_t lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int6
     int32_t c = 0;
     AP_CUDA_TRY(cudaMemcpyAsync(&c, w.ecount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AP_CUDA_TRY(cudaStreamSynchronize(s));
-    const int nb = (int)((n + 4095) / 4096);
-    colsum_rows_kernel<<<nb, 128, 0, s>>>(X, n, di, ldx, 4096, w.part);
-    colmean_rows_kernel<<<(di + 127) / 128, 128, 0, s>>>(w.part, nb, di, n, w.mean);
+    AP_TRY(column_means(X, n, di, ldx, w.part, w.mean, s));
     const int64_t npad = (n + 127) / 128 * 128;
     const int64_t cpad = ((int64_t)c + 255) / 256 * 256;
     centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
@@ -562,7 +539,7 @@ APGB_API int32_t lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int6
     centre_bf16_kernel<<<(int)std::min<int64_t>((cpad + 7) / 8, 65535), 256, 0, s>>>(
         X, ldx, di, w.epts, c, cpad, dpad, w.mean, w.Eb, w.enrm);
     AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
-    note_launches(5);
+    note_launches(3);
     AP_TRY(last_error());
     AP_TRY(tc_assign_argmax(w.Xb, (int)n, w.Eb, c, w.enrm, dpad, w.arg, nullptr, w.err, s));
     const int lgrid = (int)std::min<int64_t>((n + 255) / 256, 4096);
@@ -784,15 +761,13 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
         AP_CUDA_TRY(cudaMemsetAsync(w.maxd, 0, sizeof(unsigned) * c, s));
         max_distance_kernel<<<(int)((Ll + 255) / 256), 256, 0, s>>>(w.lap.SL, ld32(Ll), w.lap.idxL, w.slot,
                                                                      Ll, w.maxd);
-        const int nb = (int)((nl + 4095) / 4096);
-        colsum_rows_kernel<<<nb, 128, 0, s>>>(Xl, nl, di, ldl, 4096, w.lap.part);
-        colmean_rows_kernel<<<(di + 127) / 128, 128, 0, s>>>(w.lap.part, nb, di, nl, w.lap.mean);
+        AP_TRY(column_means(Xl, nl, di, ldl, w.lap.part, w.lap.mean, s));
         const int64_t npad = (nl + 127) / 128 * 128, cpad = ((int64_t)c + 255) / 256 * 256;
         centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
             Xl, ldl, di, nullptr, nl, npad, dpad, w.lap.mean, w.lap.Xb, w.xnrm);
         centre_bf16_kernel<<<(int)std::min<int64_t>((cpad + 7) / 8, 65535), 256, 0, s>>>(
             Xl, ldl, di, w.lap.epts, c, cpad, dpad, w.lap.mean, w.lap.Eb, w.lap.enrm);
-        note_launches(7);
+        note_launches(5);
         AP_TRY(last_error());
         AP_TRY(tc_assign_argmax(w.lap.Xb, (int)nl, w.lap.Eb, c, w.lap.enrm, dpad, w.lap.arg, w.best,
                                 w.lap.err, s));
@@ -831,15 +806,13 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
     AP_CUDA_TRY(cudaStreamSynchronize(s));
     std::sort(hE.begin(), hE.end());
     AP_CUDA_TRY(cudaMemcpyAsync(w.E, hE.data(), sizeof(int32_t) * nE, cudaMemcpyHostToDevice, s));
-    const int nb = (int)((n + 4095) / 4096);
-    colsum_rows_kernel<<<nb, 128, 0, s>>>(X, n, di, ldx, 4096, w.lap.part);
-    colmean_rows_kernel<<<(di + 127) / 128, 128, 0, s>>>(w.lap.part, nb, di, n, w.lap.mean);
+    AP_TRY(column_means(X, n, di, ldx, w.lap.part, w.lap.mean, s));
     const int64_t npad = (n + 127) / 128 * 128, epad = (nE + 255) / 256 * 256;
     centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
         X, ldx, di, nullptr, n, npad, dpad, w.lap.mean, w.lap.Xb, nullptr);
     centre_bf16_kernel<<<(int)std::min<int64_t>((epad + 7) / 8, 65535), 256, 0, s>>>(
         X, ldx, di, w.E, nE, epad, dpad, w.lap.mean, w.Eb, w.enrm);
-    note_launches(4);
+    note_launches(2);
     AP_TRY(last_error());
     AP_TRY(tc_assign_argmax(w.lap.Xb, (int)n, w.Eb, (int)nE, w.enrm, dpad, w.lap.arg, nullptr,
                             w.lap.err, s));

@@ -3,6 +3,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace apgb {
 
@@ -40,7 +41,39 @@ int32_t require_sm103() {
     return cc == 103 ? AP_OK : AP_ERR_UNSUPPORTED;
 }
 
+// One CTA waits on a shared-memory mbarrier that nothing completes, with the
+// same bounded try-wait loop every wait of the library uses; when the bound
+// runs out it records the give-up and returns, with nothing in flight.
+__global__ void wait_selftest_kernel(uint32_t limit, int32_t* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = ptx::mbar_wait(&bar, 0u, limit);
+    if (threadIdx.x == 0) *status = ok ? AP_OK : AP_ERR_TIMEOUT;
+}
+
 }  // namespace apgb
+
+using namespace apgb;
+
+APGB_API int32_t ap_wait_selftest(uint32_t spin_limit, void* stream) {
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t* d = nullptr;
+    AP_CUDA_TRY(cudaMallocAsync(&d, sizeof(int32_t), s));
+    wait_selftest_kernel<<<1, 32, 0, s>>>(spin_limit, d);
+    note_launches(1);
+    int32_t h = AP_ERR_CUDA;
+    const cudaError_t e1 = cudaGetLastError();
+    const cudaError_t e2 = cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e3 = cudaFreeAsync(d, s);
+    const cudaError_t e4 = cudaStreamSynchronize(s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) return AP_ERR_CUDA;
+    return h;
+}
 
 APGB_API const char* ap_status_string(int32_t s) {
     switch (s) {

@@ -29,26 +29,26 @@ int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int
 size_t tc_similarity_pad_rows();
 
 // ---- 1. column means -----------------------------------------------------------
-// Column sums of X in float64 over blocks of kMeanRows rows.  Block: 32
+// Column sums of X in float64 over blocks of `rows` rows.  Block: 32
 // columns x 8 row lanes; lane y sums rows y, y+8, ... of the row block, and
 // the 8 lane sums are added in a fixed tree (deterministic).  Grid:
-// (ceil(d/32), ceil(n/kMeanRows)).  part[row block][j].
+// (ceil(d/32), ceil(n/rows)).  part[row block][j].
 constexpr int kMeanRows = 256;
 
-__global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ X, int n, int d,
-                                                             int64_t ldx, double* part) {
+__global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ X, int64_t n, int d,
+                                                             int64_t ldx, int64_t rows, double* part) {
     const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + cx;
-    const int r0 = blockIdx.y * kMeanRows;
-    const int r1 = min(n, r0 + kMeanRows);
+    const int64_t r0 = (int64_t)blockIdx.y * rows;
+    const int64_t r1 = min(n, r0 + rows);
     __shared__ double ps[8][32];
     // Neumaier-compensated float32 sum of the lane's rows (float64 arithmetic is
     // scarce on this part); (s, c) carries the sum to well below float32 rounding
     float sm = 0.f, cm = 0.f;
     if (j < d) {
 #pragma unroll 8
-        for (int i = r0 + ry; i < r1; i += 8) {
-            const float x = X[(int64_t)i * ldx + j];
+        for (int64_t i = r0 + ry; i < r1; i += 8) {
+            const float x = X[i * ldx + j];
             const float t = sm + x;
             cm += (fabsf(sm) >= fabsf(x)) ? (sm - t) + x : (x - t) + sm;
             sm = t;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __rest
                                             ((ps[4][cx] + ps[5][cx]) + (ps[6][cx] + ps[7][cx]));
 }
 
-__global__ void colmean_kernel(const double* __restrict__ part, int nb, int d, int n,
+__global__ void colmean_kernel(const double* __restrict__ part, int nb, int d, int64_t n,
                                float* mean) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d) return;
@@ -341,12 +341,26 @@ static int pad_rows(int n) {
     return (n + t - 1) / t * t;
 }
 static int pad_dim(int d) { return (d + 63) / 64 * 64; }
-static int mean_blocks(int n) { return (n + kMeanRows - 1) / kMeanRows; }
+// Row blocks of the column means: 256 rows, or more so that there are at most
+// 2048 blocks (the float64 combine of the partials is sequential per column).
+static int64_t mean_rows(int64_t n) { return std::max<int64_t>(kMeanRows, (n + 2047) / 2048); }
+static int mean_blocks(int64_t n) { return (int)((n + mean_rows(n) - 1) / mean_rows(n)); }
+
+size_t column_mean_part_doubles(int64_t n, int d) { return (size_t)mean_blocks(n) * (size_t)d; }
+
+int32_t column_means(const float* X, int64_t n, int d, int64_t ldx, double* part, float* mean,
+                     cudaStream_t s) {
+    const int nb = mean_blocks(n);
+    colsum_partial_kernel<<<dim3((d + 31) / 32, nb), 256, 0, s>>>(X, n, d, ldx, mean_rows(n), part);
+    colmean_kernel<<<(d + 255) / 256, 256, 0, s>>>(part, nb, d, n, mean);
+    note_launches(2);
+    return last_error();
+}
 
 static size_t carve_sim(void* ws, int64_t n, int64_t d, SimWs* w) {
     Carver c(ws);
     const int npad = pad_rows((int)n), dpad = pad_dim((int)d);
-    w->part = c.take<double>((size_t)mean_blocks((int)n) * d);
+    w->part = c.take<double>(column_mean_part_doubles(n, (int)d));
     w->mean = c.take<float>(d);
     w->xc = c.take<float>((size_t)npad * dpad);   // large enough for either precision
     w->nrm = c.take<float>(npad);
@@ -396,9 +410,7 @@ static int32_t similarity_enqueue(const float* X, int ni, int di, int64_t ldx, f
                                   double noise_rel, uint64_t seed, const SimWs& w, float* pref_dev,
                                   int32_t* err, cudaStream_t s) {
     const int npad = pad_rows(ni), dpad = pad_dim(di);
-    const int nb = mean_blocks(ni);
-    colsum_partial_kernel<<<dim3((di + 31) / 32, nb), 256, 0, s>>>(X, ni, di, ldx, w.part);
-    colmean_kernel<<<(di + 255) / 256, 256, 0, s>>>(w.part, nb, di, ni, w.mean);
+    AP_TRY(column_means(X, ni, di, ldx, w.part, w.mean, s));
     const int cgrid = std::min((npad + 7) / 8, 65535);
     if (precision == AP_PREC_FP32) {
         centre_kernel<false><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
@@ -425,7 +437,7 @@ static int32_t similarity_enqueue(const float* X, int ni, int di, int64_t ldx, f
         noise_kernel<<<std::min(ni, 8192), 256, 0, s>>>(S, ni, lds, noise_rel, seed);
         note_launches(1);
     }
-    note_launches(precision == AP_PREC_FP32 ? 5 : 4);   // means(2), centre, GEMM, diagonal
+    note_launches(precision == AP_PREC_FP32 ? 3 : 2);   // centre, GEMM, diagonal
     return last_error();
 }
 

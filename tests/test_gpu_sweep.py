@@ -348,3 +348,17 @@ def test_end_to_end_ill_conditioned_mixture_lambda05():
     nonex = np.setdiff1d(np.arange(len(idx)), E)
     assert (So[nonex, idx[nonex]] >= So[nonex, E[best[nonex]]] - 1e-3).all()
     assert ex["netsim"] >= eo["netsim"] * 1.02
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a fault: a wait on an mbarrier that nothing
+    completes runs out its bound and reports AP_ERR_TIMEOUT; afterwards the
+    device still runs the normal path correctly."""
+    from paper_0910_1650_gb300.capi import AP_ERR_TIMEOUT
+    # small bounds: each try-wait may suspend for a system-dependent time
+    assert capi.ap_wait_selftest(1 << 6) == AP_ERR_TIMEOUT
+    assert capi.ap_wait_selftest(1 << 10) == AP_ERR_TIMEOUT
+    S = workload_S("small_37")
+    R, A, res, _ = capi.ap_iterate(dev_square(S), damping=0.5, max_iter=5, conv_iter=0)
+    ref = oap.run(S, lam=0.5, fixed_iters=5)
+    assert rel_inf(host(R), ref["R"]) <= TOL and rel_inf(host(A), ref["A"]) <= TOL
