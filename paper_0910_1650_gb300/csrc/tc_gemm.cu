@@ -39,7 +39,8 @@ constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int B_BYTES = BN * BK * 2;            // 32 KB
 constexpr int OUT_COLS = 32;                    // fp32 columns per store chunk (128 B)
 constexpr int OUT_BYTES = BM * OUT_COLS * 4;    // 16 KB
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter: column halves
+constexpr int THREADS = 64 + 32 * EPI_WARPS;    // producer, MMA issuer, epilogue
 constexpr uint32_t TMEM_COLS = 512;
 
 enum Mode : int { SIM = 0, ARGMAX = 1 };
@@ -47,7 +48,9 @@ enum Mode : int { SIM = 0, ARGMAX = 1 };
 struct Smem {
     uint8_t a[STAGES][A_BYTES];
     uint8_t b[STAGES][B_BYTES];
-    uint8_t out[2][OUT_BYTES];
+    uint8_t out[2][2][OUT_BYTES];   // [column half][double buffer]
+    float hbest[BM];                // ARGMAX: the second half's row results
+    int hidx[BM];
     float bnrm[2][BN];              // |b_k|^2 of the columns of the tile, by accumulator
     uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], mma_done;
     uint32_t tmem_base;
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&sm.tfull[b], 1);
-            ptx::mbar_init(&sm.tempty[b], 4);
+            ptx::mbar_init(&sm.tempty[b], EPI_WARPS);
         }
         ptx::mbar_init(&sm.mma_done, 1);
         ptx::fence_mbar_init();
@@ -291,9 +294,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             ptx::mbar_wait(&sm.mma_done, 0, p.spin_limit);
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
+        // ---------------- epilogue (warps 2..9) ----------------
+        // Warp w reads TMEM lane quarter w % 4 (its rows) and column half
+        // (w - 2) / 4 of each 256-column accumulator: two warps per quarter.
         const int sub = warp & 3;                    // TMEM lane quarter this warp may access
-        const int et = threadIdx.x - 64;             // 0..127
+        const int half = (warp - 2) >> 2;            // column half: chunks 4*half .. 4*half+3
+        const int et = threadIdx.x - 64;             // 0..255
+        const int eth = et & 127;                    // within the half
+        const int hbar = 2 + half;                   // named barrier of the half (128 threads)
         const int row_in_tile = sub * 32 + lane;
         int acc = 0;
         uint32_t tph = 0;
@@ -307,12 +315,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tile_mn(u, q, m, n);
                 m0 = m;
                 // column norms of this tile, staged once per tile
-                for (int c = et; c < BN; c += 128) {
+                for (int c = et; c < BN; c += 32 * EPI_WARPS) {
                     const int k = n * BN + c;
                     sm.bnrm[acc][c] = (k < p.N) ? p.bnrm[k] : 0.f;
                 }
                 // one thread waits (bounded) and publishes the outcome, so that
-                // all four epilogue warps leave the loop at the same barrier
+                // all epilogue warps leave the loop at the same barrier
                 if (et == 0) {
                     const bool ok = ptx::mbar_wait(&sm.tfull[acc], (tph >> acc) & 1u, p.spin_limit);
                     if (!ok || aborted(sm)) {
@@ -321,20 +329,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
                 tph ^= 1u << acc;
-                named_barrier(1, 128);
+                named_barrier(1, 32 * EPI_WARPS);
                 if (*reinterpret_cast<volatile int*>(&sm.ep_abort)) break;
                 tc_fence_after();
                 const int i = m * BM + row_in_tile;
                 const float ai = (i < p.M) ? p.anrm[i] : 0.f;
                 const uint32_t tbase = tmem + (uint32_t)(acc * BN) + ((uint32_t)(sub * 32) << 16);
-                for (int c = 0; c < BN / OUT_COLS; ++c) {
+                for (int c = 4 * half; c < 4 * half + 4; ++c) {
                     float v[32];
                     tmem_ld32(tbase + (uint32_t)(c * OUT_COLS), v);
                     if (p.mode == SIM) {
-                        // output chunk c: wait until the store of chunk c-2 has left this buffer
-                        if (et == 0) ptx::bulk_wait_read<1>();
-                        named_barrier(1, 128);
-                        uint8_t* buf = sm.out[ob];
+                        // output chunk c: wait until this half's store of two chunks
+                        // ago has left the buffer
+                        if (eth == 0) ptx::bulk_wait_read<1>();
+                        named_barrier(hbar, 128);
+                        uint8_t* buf = sm.out[half][ob];
 #pragma unroll
                         for (int u4 = 0; u4 < 8; ++u4) {
                             float o[4];
@@ -363,8 +372,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                             }
                         }
                         ptx::fence_proxy_async_smem();
-                        named_barrier(1, 128);
-                        if (et == 0) {
+                        named_barrier(hbar, 128);
+                        if (eth == 0) {
                             if (c0 < p.n4) {
                                 tma_store_2d(&tmOut, c0, m * BM, buf);
                             }
@@ -389,14 +398,27 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (*reinterpret_cast<volatile int*>(&sm.ep_abort)) break;
             if (p.mode == ARGMAX) {
-                const int i = m0 * BM + row_in_tile;
-                if (i < p.M) {
-                    p.arg[i] = bidx;
-                    if (p.best) p.best[i] = best;
+                // merge the two column halves of each row: the larger score,
+                // the lower column on a tie
+                if (half == 1) {
+                    sm.hbest[row_in_tile] = best;
+                    sm.hidx[row_in_tile] = bidx;
                 }
+                named_barrier(1, 32 * EPI_WARPS);
+                if (half == 0) {
+                    const float b1 = sm.hbest[row_in_tile];
+                    const int i1 = sm.hidx[row_in_tile];
+                    if (b1 > best || (b1 == best && i1 < bidx)) { best = b1; bidx = i1; }
+                    const int i = m0 * BM + row_in_tile;
+                    if (i < p.M) {
+                        p.arg[i] = bidx;
+                        if (p.best) p.best[i] = best;
+                    }
+                }
+                named_barrier(1, 32 * EPI_WARPS);   // the merge area is reused next unit
             }
         }
-        if (et == 0) ptx::bulk_wait_all();
+        if (eth == 0) ptx::bulk_wait_all();
     }
 
     tc_fence_before();
