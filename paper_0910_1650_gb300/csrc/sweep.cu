@@ -178,6 +178,7 @@ sweep_kernel(SweepLaunch L) {
     const bool doA = t >= 2;
     const bool doR = t <= st->max_iter;
     const float lam = a.lam, oml = 1.0f - a.lam;
+    const float2 lam2 = make_float2(lam, lam), oml2 = make_float2(oml, oml), nom2 = make_float2(-oml, -oml);
     const float* Rin = ((t - 1) & 1) ? a.R1 : a.R0;
     float* Rout = (t & 1) ? a.R1 : a.R0;
 
@@ -269,7 +270,7 @@ sweep_kernel(SweepLaunch L) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int k = 4 * f + e;
-                    set_lane(cv[q], e, k < a.n ? a.cvec[k] : 0.f);
+                    set_lane(cv[q], e, k < a.n ? oml * a.cvec[k] : 0.f);   // (1-lambda) c(k)
                 }
             }
         }
@@ -329,24 +330,32 @@ sweep_kernel(SweepLaunch L) {
                         if (f != fi && f < f_full_end) {
                             // fast path: no diagonal, no ragged tail
                             const int k0 = 4 * f;
+                            // (1-lambda) min(0, c - max(0,r)) = min(0, (1-lambda)c - (1-lambda)max(0,r)),
+                            // in packed f32x2 arithmetic, two columns per instruction
+                            float2 alo = make_float2(a4.x, a4.y), ahi = make_float2(a4.z, a4.w);
                             if (doA) {
-                                a4.x = fmaf(lam, a4.x, oml * fminf(0.f, cv[q].x - fmaxf(0.f, r4.x)));
-                                a4.y = fmaf(lam, a4.y, oml * fminf(0.f, cv[q].y - fmaxf(0.f, r4.y)));
-                                a4.z = fmaf(lam, a4.z, oml * fminf(0.f, cv[q].z - fmaxf(0.f, r4.z)));
-                                a4.w = fmaf(lam, a4.w, oml * fminf(0.f, cv[q].w - fmaxf(0.f, r4.w)));
-                                float d;
-                                d = a4.x + r4.x; if (d > dv) { dv = d; dj = k0; }
-                                d = a4.y + r4.y; if (d > dv) { dv = d; dj = k0 + 1; }
-                                d = a4.z + r4.z; if (d > dv) { dv = d; dj = k0 + 2; }
-                                d = a4.w + r4.w; if (d > dv) { dv = d; dj = k0 + 3; }
-                                A4[x] = a4;
+                                const float2 tlo = __ffma2_rn(nom2, make_float2(fmaxf(0.f, r4.x), fmaxf(0.f, r4.y)),
+                                                              make_float2(cv[q].x, cv[q].y));
+                                const float2 thi = __ffma2_rn(nom2, make_float2(fmaxf(0.f, r4.z), fmaxf(0.f, r4.w)),
+                                                              make_float2(cv[q].z, cv[q].w));
+                                alo = __ffma2_rn(lam2, alo, make_float2(fminf(0.f, tlo.x), fminf(0.f, tlo.y)));
+                                ahi = __ffma2_rn(lam2, ahi, make_float2(fminf(0.f, thi.x), fminf(0.f, thi.y)));
+                                const float2 dlo = __fadd2_rn(alo, make_float2(r4.x, r4.y));
+                                const float2 dhi = __fadd2_rn(ahi, make_float2(r4.z, r4.w));
+                                if (dlo.x > dv) { dv = dlo.x; dj = k0; }
+                                if (dlo.y > dv) { dv = dlo.y; dj = k0 + 1; }
+                                if (dhi.x > dv) { dv = dhi.x; dj = k0 + 2; }
+                                if (dhi.y > dv) { dv = dhi.y; dj = k0 + 3; }
+                                A4[x] = make_float4(alo.x, alo.y, ahi.x, ahi.y);
                             }
                             if (doR) {
+                                const float2 vlo = __fadd2_rn(alo, make_float2(s4.x, s4.y));
+                                const float2 vhi = __fadd2_rn(ahi, make_float2(s4.z, s4.w));
                                 float v;
-                                v = a4.x + s4.x; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0; }
-                                v = a4.y + s4.y; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 1; }
-                                v = a4.z + s4.z; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 2; }
-                                v = a4.w + s4.w; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 3; }
+                                v = vlo.x; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0; }
+                                v = vlo.y; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 1; }
+                                v = vhi.x; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 2; }
+                                v = vhi.y; tp.m2 = fmaxf(tp.m2, fminf(tp.m1, v)); if (v > tp.m1) { tp.m1 = v; tp.j1 = k0 + 3; }
                             }
                         } else {
 #pragma unroll
@@ -356,9 +365,9 @@ sweep_kernel(SweepLaunch L) {
                                     const float sv = lane(s4, e), rv = lane(r4, e);
                                     float av = lane(a4, e);
                                     if (doA) {
-                                        const float an = (k == i) ? colp_i
-                                                                  : fminf(0.f, lane(cv[q], e) - fmaxf(0.f, rv));
-                                        av = fmaf(lam, av, oml * an);
+                                        const float an = (k == i) ? oml * colp_i
+                                                                  : fminf(0.f, fmaf(-oml, fmaxf(0.f, rv), lane(cv[q], e)));
+                                        av = fmaf(lam, av, an);
                                         set_lane(a4, e, av);
                                         argmax_merge(dv, dj, av + rv, k);
                                     }
@@ -430,8 +439,9 @@ sweep_kernel(SweepLaunch L) {
                 }
                 if (doR) {
                     u = top2_warp_redux(u);
-                    const float m1 = u.m1, m2 = u.m2;
+                    const float om1 = oml * u.m1, om2 = oml * u.m2;     // (1-lambda) m1, m2
                     const int j1 = u.j1;
+                    const float2 nm1 = make_float2(-om1, -om1);
                     const float4* S4 = sS(s);
                     float4* R4 = sR(s);
                     const int fi = i >> 2;
@@ -444,23 +454,26 @@ sweep_kernel(SweepLaunch L) {
                             const float4 s4 = S4[x], r4 = R4[x];
                             float4 o;
                             if (f != fi && f != fj && f < f_full_end) {
-                                // fast path: every column takes m1, none is the diagonal
-                                o.x = fmaf(lam, r4.x, oml * (s4.x - m1));
-                                o.y = fmaf(lam, r4.y, oml * (s4.y - m1));
-                                o.z = fmaf(lam, r4.z, oml * (s4.z - m1));
-                                o.w = fmaf(lam, r4.w, oml * (s4.w - m1));
-                                acc[q].x += fmaxf(0.f, o.x);
-                                acc[q].y += fmaxf(0.f, o.y);
-                                acc[q].z += fmaxf(0.f, o.z);
-                                acc[q].w += fmaxf(0.f, o.w);
+                                // fast path: every column takes m1, none is the diagonal;
+                                // lambda r + (1-lambda) s - (1-lambda) m1, packed f32x2
+                                const float2 olo = __ffma2_rn(lam2, make_float2(r4.x, r4.y),
+                                                              __ffma2_rn(oml2, make_float2(s4.x, s4.y), nm1));
+                                const float2 ohi = __ffma2_rn(lam2, make_float2(r4.z, r4.w),
+                                                              __ffma2_rn(oml2, make_float2(s4.z, s4.w), nm1));
+                                const float2 plo = __fadd2_rn(make_float2(acc[q].x, acc[q].y),
+                                                              make_float2(fmaxf(0.f, olo.x), fmaxf(0.f, olo.y)));
+                                const float2 phi = __fadd2_rn(make_float2(acc[q].z, acc[q].w),
+                                                              make_float2(fmaxf(0.f, ohi.x), fmaxf(0.f, ohi.y)));
+                                acc[q] = make_float4(plo.x, plo.y, phi.x, phi.y);
+                                o = make_float4(olo.x, olo.y, ohi.x, ohi.y);
                                 R4[x] = o;
                             } else {
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
                                     const int k = 4 * f + e;
                                     const float sv = lane(s4, e), rv = lane(r4, e);
-                                    const float m = (k == j1) ? m2 : m1;
-                                    const float rn = fmaf(lam, rv, oml * (sv - m));
+                                    const float om = (k == j1) ? om2 : om1;
+                                    const float rn = fmaf(lam, rv, fmaf(oml, sv, -om));
                                     set_lane(o, e, rn);
                                     if (k < a.n) {
                                         if (k == i) a.rkk[i] = rn;
