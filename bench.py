@@ -50,6 +50,22 @@ def _dist():
     return world, rank, local
 
 
+def aggregate(elapsed_s, bytes_done, world, device):
+    """Whole-job figures over the replicas: the slowest rank's time (max) and
+    every rank's bytes (sum), by all-reduce when world > 1.  Returns
+    (elapsed_max_s, total_bytes, value_gbs)."""
+    import torch
+    import torch.distributed as dist
+
+    times = torch.tensor([float(elapsed_s)], device=device, dtype=torch.float64)
+    tot = torch.tensor([float(bytes_done)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    t = max(float(times.item()), 1e-12)
+    return t, float(tot.item()), float(tot.item()) / t / 1e9
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -203,13 +219,7 @@ def run_gpu(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = capi.kernel_launches() - launches0
     bytes_done = 20.0 * n * n * iters
-    times = torch.tensor([elapsed], device=dev)
-    tot_bytes = torch.tensor([bytes_done], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot_bytes, op=dist.ReduceOp.SUM)
-    elapsed_max = float(times.item())
-    value = float(tot_bytes.item()) / elapsed_max / 1e9
+    elapsed_max, _, value = aggregate(elapsed, bytes_done, world, dev)
 
     # ---- end to end through the C ABI: host features in, labels out ------------
     if args.no_e2e:
@@ -229,12 +239,7 @@ def run_gpu(args):
     barrier()
     e_elapsed = ev0.elapsed_time(ev1) / 1e3
     e_wall = time.perf_counter() - e0
-    e_bytes = torch.tensor([20.0 * n * n * e_iters], device=dev, dtype=torch.float64)
-    e_t = torch.tensor([max(e_elapsed, 1e-9)], device=dev)
-    if world > 1:
-        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e_bytes, op=dist.ReduceOp.SUM)
-    e_value = float(e_bytes.item()) / float(e_t.item()) / 1e9
+    _, _, e_value = aggregate(max(e_elapsed, 1e-9), 20.0 * n * n * e_iters, world, dev)
 
     if rank == 0:
         peaks, src = _peaks()
