@@ -13,6 +13,9 @@
 //      bits), both middle order statistics at once;
 //   5. diagonal <- p, then s <- s + noise_rel*|s|*u(i,k) on every entry.
 #include <algorithm>
+#include <mutex>
+#include <map>
+#include <array>
 #include <climits>
 #include <cmath>
 
@@ -477,6 +480,38 @@ APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx
     return AP_OK;
 }
 
+namespace apgb {
+
+// Problems of a batch are spread round-robin over kSimStreams library-owned
+// streams (created once per device), each with its own workspace slice: the
+// small problems' latency-bound kernels then overlap.  They fork from and
+// join back to the caller's stream through events.
+constexpr int kSimStreams = 4;
+
+static std::mutex g_sim_mu;
+static std::map<int, std::array<cudaStream_t, kSimStreams>> g_sim_streams;
+
+static int32_t sim_streams(std::array<cudaStream_t, kSimStreams>* out) {
+    int dev = 0;
+    AP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_sim_mu);
+    auto it = g_sim_streams.find(dev);
+    if (it == g_sim_streams.end()) {
+        std::array<cudaStream_t, kSimStreams> a{};
+        for (auto& x : a) AP_CUDA_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        it = g_sim_streams.emplace(dev, a).first;
+    }
+    *out = it->second;
+    return AP_OK;
+}
+
+static size_t batched_slice(int64_t nmax, int64_t d) {
+    SimWs w;
+    return (carve_sim(nullptr, nmax, d, &w) + 255) / 256 * 256;
+}
+
+}  // namespace apgb
+
 APGB_API size_t ap_similarity_batched_workspace_size(const int64_t* n, int32_t count, int64_t d) {
     if (!n || count < 1 || d < 1 || d > 65536) return 0;
     int64_t nmax = 0;
@@ -484,9 +519,8 @@ APGB_API size_t ap_similarity_batched_workspace_size(const int64_t* n, int32_t c
         if (n[b] < 2 || n[b] > INT_MAX / 2) return 0;
         nmax = std::max(nmax, n[b]);
     }
-    SimWs w;
     Carver c(nullptr);
-    c.take<unsigned char>(carve_sim(nullptr, nmax, d, &w));
+    c.take<unsigned char>(batched_slice(nmax, d) * kSimStreams);
     c.take<float>((size_t)count);
     return c.used;
 }
@@ -509,22 +543,52 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
     AP_TRY(require_sm103());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AP_TRY(check_ws(ws, ws_bytes, ap_similarity_batched_workspace_size(n, count, d)));
-    SimWs w;
+    std::array<cudaStream_t, kSimStreams> ss;
+    AP_TRY(sim_streams(&ss));
+    const size_t slice = batched_slice(nmax, d);
     Carver c(ws);
-    c.take<unsigned char>(carve_sim(nullptr, nmax, d, &w));
-    carve_sim(ws, nmax, d, &w);
+    unsigned char* base = c.take<unsigned char>(slice * kSimStreams);
     float* prefs = c.take<float>((size_t)count);
-    AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
-    for (int32_t b = 0; b < count; ++b)
-        AP_TRY(similarity_enqueue(X + xoff[b], (int)n[b], (int)d, ldx, S + soff[b], lds[b], precision,
-                                  pref_mode, pref, 0.0, 0, w, prefs + b, w.err, s));
+    SimWs w[kSimStreams];
+    for (int k = 0; k < kSimStreams; ++k) {
+        carve_sim(base + slice * k, nmax, d, &w[k]);
+        AP_CUDA_TRY(cudaMemsetAsync(w[k].err, 0, sizeof(int32_t), s));
+    }
+    // fork: every worker stream starts after the caller's earlier work
+    cudaEvent_t fork, join[kSimStreams];
+    AP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (auto& e : join) AP_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    struct Guard {
+        cudaEvent_t f;
+        cudaEvent_t* j;
+        ~Guard() {
+            cudaEventDestroy(f);
+            for (int k = 0; k < kSimStreams; ++k) cudaEventDestroy(j[k]);
+        }
+    } guard{fork, join};
+    AP_CUDA_TRY(cudaEventRecord(fork, s));
+    for (int k = 0; k < kSimStreams; ++k) AP_CUDA_TRY(cudaStreamWaitEvent(ss[k], fork, 0));
+    int32_t st = AP_OK;
+    for (int32_t b = 0; b < count && st == AP_OK; ++b) {
+        const int k = b % kSimStreams;
+        st = similarity_enqueue(X + xoff[b], (int)n[b], (int)d, ldx, S + soff[b], lds[b], precision,
+                                pref_mode, pref, 0.0, 0, w[k], prefs + b, w[k].err, ss[k]);
+    }
+    // join: the caller's stream continues after every worker (also on error)
+    for (int k = 0; k < kSimStreams; ++k) {
+        AP_CUDA_TRY(cudaEventRecord(join[k], ss[k]));
+        AP_CUDA_TRY(cudaStreamWaitEvent(s, join[k], 0));
+    }
+    AP_TRY(st);
     std::vector<float> v(count, pref_mode == AP_PREF_SCALAR ? pref[0] : NAN);
-    int32_t err = 0;
+    int32_t err[kSimStreams] = {0};
     if (pref_mode == AP_PREF_MEDIAN)
         AP_CUDA_TRY(cudaMemcpyAsync(v.data(), prefs, sizeof(float) * count, cudaMemcpyDeviceToHost, s));
-    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    for (int k = 0; k < kSimStreams; ++k)
+        AP_CUDA_TRY(cudaMemcpyAsync(&err[k], w[k].err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AP_CUDA_TRY(cudaStreamSynchronize(s));
-    if (err) return AP_ERR_TIMEOUT;
+    for (int k = 0; k < kSimStreams; ++k)
+        if (err[k]) return AP_ERR_TIMEOUT;
     if (pref_out)
         for (int32_t b = 0; b < count; ++b) pref_out[b] = v[b];
     return AP_OK;
