@@ -8,20 +8,30 @@
 // Operands are bf16, K-major, loaded by TMA with 128-byte swizzle; the
 // product accumulates in fp32 in tensor memory.
 //
-// Persistent, warp-specialised kernel (one CTA per SM, 192 threads):
-//   warp 0      TMA producer: A (128 x 64) and B (256 x 64) tiles into a
-//               3-stage shared-memory ring (mbarriers full/empty);
+// Persistent, warp-specialised kernel (one CTA per SM, 320 threads), launched
+// as clusters of two CTAs that compute vertically adjacent tiles (row blocks
+// 2p and 2p+1) against the same column block:
+//   warp 0      TMA producer: this CTA's A tile (128 x 64) and one half of the
+//               shared B tile (128 of its 256 rows), the half multicast into
+//               both CTAs' shared memory, into a 3-stage ring (mbarriers
+//               full/empty); a stage is refilled once both CTAs' MMAs have
+//               released it (their commits are multicast onto both "empty"s);
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma
 //               (M=128, N=256, K=16) from one elected thread into two
 //               256-column accumulators (mbarriers tfull/tempty);
-//   warps 2..5  epilogue: tcgen05.ld of its 32 rows, the fused arithmetic,
-//               then either swizzled shared memory -> TMA tensor store
-//               (similarity) or a running per-row arg-max (assignment).
+//   warps 2..9  epilogue, two warps per TMEM lane quarter (column halves):
+//               tcgen05.ld, the fused arithmetic, then either swizzled shared
+//               memory -> TMA tensor store (similarity) or a running per-row
+//               arg-max (assignment).
+// Multicasting the shared operand cuts each CTA's operand stream from 48 KB
+// to 32 KB per K step.
 // Every mbarrier wait is bounded; on expiry the kernel records an error and
 // all roles stop issuing new work.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <climits>
@@ -92,6 +102,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// The same load delivered to the same shared-memory offset (and mbarrier) of
+// every CTA of the cluster in `mask`.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
+                                               uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(ptx::smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(ptx::smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                      map),
@@ -127,6 +148,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives on `bar` of every CTA in `mask` once every tcgen05.mma issued so far
+// by this thread is done.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(ptx::smem_u32(bar)), "h"(mask)
         : "memory");
 }
 
@@ -189,18 +219,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+    const int crank = (int)cluster.block_rank();          // 0 or 1: row block 2p + crank
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    constexpr uint16_t kPair = 0x3;                        // both CTAs of the cluster
 
     const int numM = (p.M + BM - 1) / BM;
+    const int numMp = (numM + 1) / 2;                      // row-block pairs
     const int numN = (p.N + BN - 1) / BN;
     const int numK = p.K / BK;
-    // work units: one tile (SIM) or one row block with all its column tiles (ARGMAX)
-    const int units = (p.mode == SIM) ? numM * numN : numM;
+    // work units of a pair: one tile pair (SIM) or one row-block pair with all
+    // its column tiles (ARGMAX); a pair's second row block may lie past the end
+    // (zero-filled loads, no outputs)
+    const int units = (p.mode == SIM) ? numMp * numN : numMp;
     const int tiles_per_unit = (p.mode == SIM) ? 1 : numN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             ptx::mbar_init(&sm.full[s], 1);
-            ptx::mbar_init(&sm.empty[s], 1);
+            ptx::mbar_init(&sm.empty[s], 2);               // one commit from each CTA's MMAs
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&sm.tfull[b], 1);
@@ -214,12 +251,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 1) tmem_alloc(&sm.tmem_base, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
+    cluster.sync();                                        // the peer's barriers exist
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
 
     auto tile_mn = [&](int u, int q, int& m, int& n) {
-        if (p.mode == SIM) { m = u / numN; n = u % numN; }
-        else { m = u; n = q; }
+        if (p.mode == SIM) { m = 2 * (u / numN) + crank; n = u % numN; }
+        else { m = 2 * u + crank; n = q; }
     };
 
     if (warp == 0) {
@@ -229,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t eph = 0x7u;                    // empty barriers start "released"
             uint32_t armed = 0;                     // loads issued per stage (low bit = parity)
             int nissued = 0;
-            for (int u = blockIdx.x; u < units && !aborted(sm); u += gridDim.x) {
+            for (int u = pair; u < units && !aborted(sm); u += npairs) {
                 for (int q = 0; q < tiles_per_unit && !aborted(sm); ++q) {
                     int m, n;
                     tile_mn(u, q, m, n);
@@ -240,8 +278,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                         eph ^= 1u << stage;
                         ptx::mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
+                        // own A tile; this CTA's half of the shared B tile, into both CTAs
                         tma_load_2d(sm.a[stage], &tmA, kb * BK, m * BM, &sm.full[stage]);
-                        tma_load_2d(sm.b[stage], &tmB, kb * BK, n * BN, &sm.full[stage]);
+                        tma_load_2d_mc(sm.b[stage] + crank * (B_BYTES / 2), &tmB, kb * BK,
+                                       n * BN + crank * (BN / 2), &sm.full[stage], kPair);
                         armed ^= 1u << stage;
                         ++nissued;
                         stage = (stage + 1) % STAGES;
@@ -258,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             constexpr uint32_t idesc = instr_desc(BM, BN);
             int stage = 0, acc = 0;
             uint32_t fph = 0, tph = 3;              // tempty barriers start "released"
-            for (int u = blockIdx.x; u < units && !aborted(sm); u += gridDim.x) {
+            for (int u = pair; u < units && !aborted(sm); u += npairs) {
                 for (int q = 0; q < tiles_per_unit && !aborted(sm); ++q) {
                     if (!ptx::mbar_wait(&sm.tempty[acc], (tph >> acc) & 1u, p.spin_limit)) {
                         atomicExch(&sm.abort, 1);
@@ -282,7 +322,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                             mma_bf16(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc,
                                      (kb > 0 || k > 0) ? 1u : 0u);
                         }
-                        mma_commit(&sm.empty[stage]);  // frees the stage when the MMAs are done
+                        // frees the stage (in both CTAs: the peer's B half lands in it too)
+                        mma_commit_mc(&sm.empty[stage], kPair);
                         stage = (stage + 1) % STAGES;
                     }
                     mma_commit(&sm.tfull[acc]);        // accumulator ready for the epilogue
@@ -306,7 +347,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int acc = 0;
         uint32_t tph = 0;
         int ob = 0;
-        for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        for (int u = pair; u < units; u += npairs) {
             float best = -INFINITY;
             int bidx = INT_MAX;
             int m0 = 0;
@@ -423,6 +464,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
+    // neither CTA leaves while the other may still multicast into it or
+    // arrive on its barriers
+    cluster.sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
@@ -466,8 +510,52 @@ static int32_t launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensor
     AP_TRY(device_sm_count(&sms));
     AP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_BYTES));
-    const int grid = std::max(1, std::min(units, sms));
-    tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a, b, o, p);
+    // clusters of two CTAs over row-block pairs, as many as can be resident
+    // at once (persistent: each takes every `pairs`-th unit)
+    static std::mutex mu;
+    static int resident[64] = {0};
+    int dev = 0;
+    AP_CUDA_TRY(cudaGetDevice(&dev));
+    int cap = sms / 2;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev >= 0 && dev < 64) {
+            if (resident[dev] == 0) {
+                cudaLaunchConfig_t q = {};
+                q.gridDim = dim3(2, 1, 1);
+                q.blockDim = dim3(THREADS, 1, 1);
+                q.dynamicSmemBytes = SMEM_BYTES;
+                cudaLaunchAttribute qa;
+                qa.id = cudaLaunchAttributeClusterDimension;
+                qa.val.clusterDim.x = 2;
+                qa.val.clusterDim.y = 1;
+                qa.val.clusterDim.z = 1;
+                q.attrs = &qa;
+                q.numAttrs = 1;
+                int num = 0;
+                if (cudaOccupancyMaxActiveClusters(&num, tc_gemm_kernel, &q) != cudaSuccess || num < 1) {
+                    cudaGetLastError();
+                    num = sms / 2;
+                }
+                resident[dev] = num;
+            }
+            cap = std::min(cap, resident[dev]);
+        }
+    }
+    const int pairs = std::max(1, std::min(units, cap));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * pairs, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    AP_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_gemm_kernel, a, b, o, p));
     note_launches(1);
     return last_error();
 }
@@ -487,7 +575,7 @@ int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int
     AP_TRY(make_map(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)Xb, dpad, npad, (uint64_t)dpad * 2,
                     BK, BM, CU_TENSOR_MAP_SWIZZLE_128B));
     AP_TRY(make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)Xb, dpad, npad, (uint64_t)dpad * 2,
-                    BK, BN, CU_TENSOR_MAP_SWIZZLE_128B));
+                    BK, BN / 2, CU_TENSOR_MAP_SWIZZLE_128B));
     const int n4 = n & ~3;
     AP_TRY(make_map(&mo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, S, (uint64_t)std::max(n4, 4), (uint64_t)n,
                     (uint64_t)lds * 4, OUT_COLS, BM, CU_TENSOR_MAP_SWIZZLE_128B));
@@ -504,7 +592,7 @@ int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int
     p.lds = lds;
     p.spin_limit = 1u << 22;
     p.error = err;
-    const int units = ((n + BM - 1) / BM) * ((n + BN - 1) / BN);
+    const int units = (((n + BM - 1) / BM + 1) / 2) * ((n + BN - 1) / BN);   // tile pairs
     return launch(ma, mb, mo, p, units, s);
 }
 
@@ -521,7 +609,7 @@ int32_t tc_assign_argmax(const __nv_bfloat16* A, int na, const __nv_bfloat16* B,
     AP_TRY(make_map(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)A, dpad, arows, (uint64_t)dpad * 2,
                     BK, BM, CU_TENSOR_MAP_SWIZZLE_128B));
     AP_TRY(make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (void*)B, dpad, brows, (uint64_t)dpad * 2,
-                    BK, BN, CU_TENSOR_MAP_SWIZZLE_128B));
+                    BK, BN / 2, CU_TENSOR_MAP_SWIZZLE_128B));
     Params p{};
     p.M = na;
     p.N = nb;
@@ -533,7 +621,7 @@ int32_t tc_assign_argmax(const __nv_bfloat16* A, int na, const __nv_bfloat16* B,
     p.best = best;
     p.spin_limit = 1u << 22;
     p.error = err;
-    return launch(ma, mb, ma, p, (na + BM - 1) / BM, s);
+    return launch(ma, mb, ma, p, ((na + BM - 1) / BM + 1) / 2, s);         // row-block pairs
 }
 
 }  // namespace apgb
