@@ -75,9 +75,9 @@ typedef struct ap_params {
  * (the iterations are then enqueued as separate launches). */
 #define AP_FLAG_TIME_SWEEP 1
 /* ap_params.flags: enqueue iterations as separate kernel launches.  By default
- * each chunk of check_every iterations (m sweep + m column-sum launches) is
- * one CUDA graph: captured on a library-owned stream the first time a
- * workspace address and launch shape are seen, kept (up to 32 per process),
+ * each chunk of check_every iterations (m sweep + m column-sum launches, when
+ * m >= 4) is one CUDA graph: captured on a library-owned stream the first time
+ * a workspace address and launch shape are seen, kept (up to 32 per process),
  * and launched on the caller's stream. */
 #define AP_FLAG_NO_GRAPH   2
 /* ap_params.flags, pap_run only: Step 4 starts from the block-diagonal R of

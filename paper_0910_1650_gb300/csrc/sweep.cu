@@ -536,6 +536,7 @@ __global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const Sw
     const int cx = threadIdx.x % kFinCols, gy = threadIdx.x / kFinCols;
     const int k = blockIdx.x * kFinCols + cx;
     SweepState* st = a.st;
+    if (st->done) return;                       // uniform per problem; finished rows are final
     __shared__ float part[kFinLanes][kFinCols];
     float s = 0.f;
     if (k < a.n) {
@@ -770,6 +771,31 @@ struct Plan {
     int nmax = 0;
 };
 
+// The resident clusters split between the active problems by work (n^2):
+// each active problem gets at least one and at most min(n, resident);
+// finished problems get none (their rows are done).  Clusters are numbered in
+// problem order.
+static void split_clusters(const Problem* P, int count, const std::vector<char>& active,
+                           int resident, Plan* plan) {
+    double work = 0.0;
+    int nact = 0;
+    for (int b = 0; b < count; ++b)
+        if (active[b]) {
+            work += (double)P[b].n * (double)P[b].n;
+            ++nact;
+        }
+    plan->G.assign(count, 0);
+    plan->clusters = 0;
+    for (int b = 0; b < count; ++b) {
+        if (!active[b]) continue;
+        const int cap = std::max(1, std::min<int>(resident, (int)P[b].n));
+        int g = (nact == 1) ? cap : (int)std::lround((double)P[b].n * (double)P[b].n / work * resident);
+        g = std::max(1, std::min(g, cap));
+        plan->G[b] = g;
+        plan->clusters += g;
+    }
+}
+
 static int32_t make_plan(const Problem* P, int count, const SweepConfig* forced, Plan* plan) {
     int64_t nmax = 0;
     double work = 0.0;
@@ -780,17 +806,9 @@ static int32_t make_plan(const Problem* P, int count, const SweepConfig* forced,
     plan->nmax = (int)nmax;
     if (forced) plan->c = *forced;
     else AP_TRY(choose_config((int)nmax, &plan->c));
-    const int resident = std::max(plan->c.G, 1);
-    plan->G.resize(count);
-    plan->clusters = 0;
-    for (int b = 0; b < count; ++b) {
-        const double share = (double)P[b].n * (double)P[b].n / work;
-        int g = (int)std::lround(share * resident);
-        g = std::max(1, std::min<int>(g, (int)P[b].n));
-        if (count == 1) g = std::max(1, std::min<int>(resident, (int)P[b].n));
-        plan->G[b] = g;
-        plan->clusters += g;
-    }
+    (void)work;
+    std::vector<char> active(count, 1);
+    split_clusters(P, count, active, std::max(plan->c.G, 1), plan);
     return AP_OK;
 }
 
@@ -825,7 +843,8 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
         a.ns = plan.c.NS;
         a.spin_limit = 1u << 20;
         a.R1 = cv.take<float>((size_t)n * ld);
-        a.pcol = cv.take<float>((size_t)a.G * n);
+        // room for every resident cluster: the split is redone as problems finish
+        a.pcol = cv.take<float>((size_t)std::max(1, std::min<int>(std::max(plan.c.G, 1), (int)n)) * n);
         a.colp = cv.take<float>(n);
         a.cvec = cv.take<float>(n);
         a.rkk = cv.take<float>(n);
@@ -981,17 +1000,23 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
         if (hs[b].nonfinite) return AP_ERR_NONFINITE;
 
     // iterations per host check: about 4 ms of sweeping at full bandwidth
-    double elems = 0.0;
-    for (int b = 0; b < count; ++b) elems += (double)P[b].n * (double)P[b].n;
-    int chunk = p->check_every;
-    if (chunk <= 0) {
+    std::vector<char> active(count, 1);
+    auto chunk_for = [&]() {
+        if (p->check_every > 0) return (int)p->check_every;
+        double elems = 0.0;
+        for (int b = 0; b < count; ++b)
+            if (active[b]) elems += (double)P[b].n * (double)P[b].n;
         const double t_iter = 20.0 * elems / 6.0e12 + 6e-6;
-        chunk = (int)std::min(64.0, std::max(1.0, 4e-3 / t_iter));
-    }
+        return (int)std::min(64.0, std::max(1.0, 4e-3 / t_iter));
+    };
+    int chunk = chunk_for();
     const int64_t total = (int64_t)p->max_iter + 1;
     const bool timed = (p->flags & AP_FLAG_TIME_SWEEP) != 0;
     EventPairs ev;
-    if (timed) AP_TRY(ev.reserve(chunk));
+    if (timed) AP_TRY(ev.reserve(std::max(chunk, 64)));
+    // the launch plan in force: re-split between the problems still running
+    // whenever one finishes, so that no cluster idles on a finished problem
+    Plan cur = plan;
     SweepLaunch L{w.table, count};
     int64_t launched = 0;
     int32_t worked = 0;
@@ -1001,12 +1026,13 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     const bool graph = !timed && !(p->flags & AP_FLAG_NO_GRAPH);
     while (launched < total) {
         const int64_t m = std::min<int64_t>(chunk, total - launched);
-        if (graph) {
-            AP_TRY(launch_chunk_graph(c, plan, L, m, fin_grid, s));
+        // a graph pays for its capture only over several iterations
+        if (graph && m >= 4) {
+            AP_TRY(launch_chunk_graph(c, cur, L, m, fin_grid, s));
         } else {
             for (int64_t j = 0; j < m; ++j) {
                 if (timed) AP_CUDA_TRY(cudaEventRecord(ev.start[j], s));
-                AP_TRY(launch_sweep(c, plan.clusters, L, s));
+                AP_TRY(launch_sweep(c, cur.clusters, L, s));
                 if (timed) AP_CUDA_TRY(cudaEventRecord(ev.stop[j], s));
                 finalize_kernel<<<fin_grid, kFinCols * kFinLanes, 0, s>>>(w.table);
             }
@@ -1033,6 +1059,27 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
             }
         }
         if (all_done) break;
+        if (count > 1) {
+            bool changed = false;
+            for (int b = 0; b < count; ++b)
+                if (active[b] && hs[b].done) {
+                    active[b] = 0;
+                    changed = true;
+                }
+            if (changed) {
+                split_clusters(P, count, active, std::max(c.G, 1), &cur);
+                int cb = 0;
+                for (int b = 0; b < count; ++b) {
+                    w.host[b].cluster_begin = cb;
+                    w.host[b].G = cur.G[b];
+                    cb += cur.G[b];
+                }
+                // nothing is in flight (the states were just read back)
+                AP_CUDA_TRY(cudaMemcpyAsync(w.table, w.host.data(), sizeof(SweepArgs) * count,
+                                            cudaMemcpyHostToDevice, s));
+                chunk = std::min(chunk_for(), timed ? 64 : 1 << 30);
+            }
+        }
     }
     if (!all_done) return AP_ERR_CUDA;   // cannot happen: launch max_iter+1 always stops
     int32_t worst = AP_OK;
