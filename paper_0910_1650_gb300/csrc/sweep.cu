@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <array>
 #include <climits>
+#include <cmath>
 #include <functional>
 #include <map>
 #include <mutex>
@@ -69,33 +70,68 @@ struct SweepArgs {
     int          n;
     int          n4;       // float4 columns spanning n
     int          w4;       // float4 columns per CTA
-    int          cluster_begin;   // first cluster of the grid assigned to this problem
-    int          G;        // clusters assigned to this problem
+    int          G;        // units of this problem (unit g owns column-partial slot g)
     int          ns;       // pipeline stages (launch-wide)
     float        lam;      // launch-wide
     uint32_t     spin_limit;      // launch-wide
     const float* cvec;     // r(k,k) + colp(k) of R_{t-1}
     const float* colp;     // colp(k) of R_{t-1}
-    float*       pcol;     // [clusters][n] partial column sums of R_t
+    float*       pcol;     // [G][pstride] per-unit partial column sums of R_t
+    int64_t      pstride;
     float*       rkk;      // r(k,k) of R_t
     int32_t*     eflag;    // exemplar flags of the previous decisions
     int32_t*     dec;      // decisions (may be null)
     SweepState*  st;
 };
 
-struct SweepLaunch {
-    const SweepArgs* table;   // device, sorted by cluster_begin
-    int count;
+// One unit of a launch's work list: rows first, first + stride, ... (count
+// rows) of problem b, whose column partials go to the problem's slot g.
+struct __align__(16) Unit {
+    int b, g, first, count, stride, pad[3];
 };
 
-// The problem whose clusters include global cluster `gc` (binary search).
-__device__ __forceinline__ int find_instance(const SweepLaunch& L, int gc) {
-    int lo = 0, hi = L.count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (L.table[mid].cluster_begin <= gc) lo = mid; else hi = mid - 1;
-    }
-    return lo;
+// A launch's work list: cluster c runs units ubeg[c] .. ubeg[c+1]-1 one after
+// another.
+struct SweepLaunch {
+    const SweepArgs* table;   // device
+    const Unit* units;        // grouped by cluster
+    const int* ubeg;          // clusters + 1 entries
+    int count;
+    int w4s;                  // stage stride: the widest slice of the launch (float4)
+    int ns;                   // pipeline stages
+};
+
+// What a unit's CTA needs about its problem and its column slice.
+struct UnitView {
+    const SweepArgs* a;                 // read in place: fields used once per row or less
+    SweepState* st;
+    int g, first, stride, t;
+    bool doA, doR;
+    const float* Rin;
+    float* Rout;
+    int f_begin, f_end, nslice, f_full_end, nfull, nrows;
+};
+
+__device__ __forceinline__ bool unit_view(const SweepLaunch& L, int u, int crank, UnitView& v) {
+    const Unit un = L.units[u];
+    v.a = &L.table[un.b];
+    v.st = v.a->st;
+    if (v.st->done) return false;       // fixed during a launch: every CTA of the cluster agrees
+    v.g = un.g;
+    v.first = un.first;
+    v.stride = un.stride;
+    v.t = v.st->t;
+    v.doA = v.t >= 2;
+    v.doR = v.t <= v.st->max_iter;
+    v.Rin = ((v.t - 1) & 1) ? v.a->R1 : v.a->R0;
+    v.Rout = (v.t & 1) ? v.a->R1 : v.a->R0;
+    v.f_begin = crank * v.a->w4;
+    v.f_end = min(v.f_begin + v.a->w4, v.a->n4);
+    v.nslice = max(0, v.f_end - v.f_begin);
+    v.f_full_end = min(v.f_end, v.a->n >> 2);         // float4s entirely inside n
+    v.nfull = max(0, v.f_full_end - v.f_begin);
+    v.nrows = un.count;
+    return true;
 }
 
 // A warp's partial row result, exchanged across the cluster: the top-2
@@ -109,22 +145,21 @@ struct __align__(16) Slot {
 constexpr int kMaxStages = 4;
 constexpr int kMaxCluster = 16;
 
-// Row partials rotate through kXBuf buffers (by row mod kXBuf).  A warp sends
-// row r's partial after it has received every warp's partial of row r-2 (it
-// waited for them while finishing row r-2), and every warp sends its row r-2
-// partial only after it has read its slots of row r-4 (and the receiving
+// Row partials rotate through kXBuf exchange buffers, row by row.  A warp
+// sends row r's partial after it has received every warp's partial of row r-2
+// (it waited for them while finishing row r-2), and every warp sends its row
+// r-2 partial only after it has read its slots of row r-4 (and the receiving
 // barrier's phase for row r-4 has completed); so four buffers are never
 // overwritten unread.
 constexpr int kXBuf = 4;
 
-// Followed in shared memory by the row partials, kXBuf x C (sender CTA) x
-// T/32 (sender warp) Slots, then as many decision indices (int).
+// Followed in shared memory by the kXBuf exchange barriers, then the row
+// partials, kXBuf x C (sender CTA) x T/32 (sender warp) Slots, then as many
+// decision indices (int).
 struct __align__(16) Ctl {
     uint64_t full[kMaxStages];     // stage filled by TMA
     uint64_t done[kMaxStages];     // every compute warp finished with the stage
-    uint64_t xbar[kXBuf];          // every warp's partial of a row arrived
     int abort;                     // a compute warp gave up (stops the producer)
-    int cnt_changes, cnt_ex;
 };
 
 __device__ __forceinline__ float lane(const float4& v, int e) {
@@ -158,133 +193,113 @@ sweep_kernel(SweepLaunch L) {
     const int csize = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
     const int gc = blockIdx.x / csize;
-    const SweepArgs a = L.table[find_instance(L, gc)];
-    const int g = gc - a.cluster_begin;
-    const int G = a.G;
+    const int u_begin = L.ubeg[gc], u_end = L.ubeg[gc + 1];
     const int T = (int)blockDim.x - 32;         // compute threads
     const int tid = threadIdx.x;
     const int wid = tid >> 5, lid = tid & 31;
     const int nw = T >> 5;                      // compute warps
-    const int NS = a.ns;
-    const int w4 = a.w4;
+    const int NS = L.ns;
+    const int w4s = L.w4s;
+    constexpr int XB = kXBuf;
     float4* stage = reinterpret_cast<float4*>(smem);
-    Ctl* ctl = reinterpret_cast<Ctl*>(smem + (size_t)NS * 3 * w4 * sizeof(float4));
-    Slot* xs = reinterpret_cast<Slot*>(ctl + 1);
-    int* xdj = reinterpret_cast<int*>(xs + (size_t)kXBuf * csize * nw);
-
-    SweepState* st = a.st;
-    const int t = st->t;
-    if (st->done) return;                       // uniform across the grid
-    const bool doA = t >= 2;
-    const bool doR = t <= st->max_iter;
-    const float lam = a.lam, oml = 1.0f - a.lam;
-    const float2 lam2 = make_float2(lam, lam), oml2 = make_float2(oml, oml), nom2 = make_float2(-oml, -oml);
-    const float* Rin = ((t - 1) & 1) ? a.R1 : a.R0;
-    float* Rout = (t & 1) ? a.R1 : a.R0;
-
-    const int f_begin = crank * w4;
-    const int f_end = min(f_begin + w4, a.n4);
-    const int nslice = max(0, f_end - f_begin);
-    const int f_full_end = min(f_end, a.n >> 2);          // float4s entirely inside n
-    const int nfull = max(0, f_full_end - f_begin);
-    const int nrows = (g < a.n) ? (a.n - g + G - 1) / G : 0;
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem + (size_t)NS * 3 * w4s * sizeof(float4));
+    uint64_t* xbar = reinterpret_cast<uint64_t*>(ctl + 1);   // every warp's partial of a row arrived
+    Slot* xs = reinterpret_cast<Slot*>(xbar + XB);
+    int* xdj = reinterpret_cast<int*>(xs + (size_t)XB * csize * nw);
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             ptx::mbar_init(&ctl->full[s], 1);
             ptx::mbar_init(&ctl->done[s], (uint32_t)nw);
         }
-        for (int b = 0; b < kXBuf; ++b) ptx::mbar_init(&ctl->xbar[b], 1);
+        for (int b = 0; b < XB; ++b) ptx::mbar_init(&xbar[b], 1);
         ptx::fence_mbar_init();
         ctl->abort = 0;
-        ctl->cnt_changes = 0;
-        ctl->cnt_ex = 0;
     }
     __syncthreads();
     if (csize > 1) cluster.sync();              // peers' barriers exist before any st.async
 
-    auto sS = [&](int s) { return stage + ((size_t)s * 3 + 0) * w4; };
-    auto sR = [&](int s) { return stage + ((size_t)s * 3 + 1) * w4; };
-    auto sA = [&](int s) { return stage + ((size_t)s * 3 + 2) * w4; };
+    auto sS = [&](int s) { return stage + ((size_t)s * 3 + 0) * w4s; };
+    auto sR = [&](int s) { return stage + ((size_t)s * 3 + 1) * w4s; };
+    auto sA = [&](int s) { return stage + ((size_t)s * 3 + 2) * w4s; };
 
     int bad = 0;                                // a wait of this thread ran out
     if (wid == nw) {
         // ------------------------------ producer warp ------------------------------
         if (lid == 0) {
-            const uint32_t slice_bytes = (uint32_t)nslice * 16u;
-            const uint32_t row_bytes = slice_bytes * (doR ? 3u : 2u);
-            int issued = 0;
-            auto issue = [&](int r) {
-                const int s = r % NS;
-                ptx::mbar_arrive_expect_tx(&ctl->full[s], row_bytes);
-                if (nslice > 0) {
-                    const int64_t off = (int64_t)(g + r * G) * a.ld + 4 * (int64_t)f_begin;
-                    if (doR) ptx::bulk_g2s(sS(s), a.S + off, slice_bytes, &ctl->full[s]);
-                    ptx::bulk_g2s(sR(s), Rin + off, slice_bytes, &ctl->full[s]);
-                    ptx::bulk_g2s(sA(s), a.A + off, slice_bytes, &ctl->full[s]);
+            int q0 = 0;                         // rows of this cluster's earlier units
+            int sw = 0;                         // stage of the next row to store
+            uint32_t wpar = 0;                  // and the parity of its done barrier's phase
+            bool first = true;
+            for (int u = u_begin; u < u_end; ++u) {
+                UnitView v;
+                if (!unit_view(L, u, crank, v)) continue;
+                const SweepArgs& a = *v.a;
+                const uint32_t slice_bytes = (uint32_t)v.nslice * 16u;
+                const uint32_t row_bytes = slice_bytes * (v.doR ? 3u : 2u);
+                // the previous unit's stores no longer read the stages about to be refilled
+                if (!first) ptx::bulk_wait_read<0>();
+                first = false;
+                int issued = 0;
+                auto issue = [&](int r, int s) {
+                    ptx::mbar_arrive_expect_tx(&ctl->full[s], row_bytes);
+                    if (v.nslice > 0) {
+                        const int64_t off = (int64_t)(v.first + r * v.stride) * a.ld + 4 * (int64_t)v.f_begin;
+                        if (v.doR) ptx::bulk_g2s(sS(s), a.S + off, slice_bytes, &ctl->full[s]);
+                        ptx::bulk_g2s(sR(s), v.Rin + off, slice_bytes, &ctl->full[s]);
+                        ptx::bulk_g2s(sA(s), a.A + off, slice_bytes, &ctl->full[s]);
+                    }
+                    issued = r + 1;
+                };
+                for (int r = 0, s = sw; r < min(NS, v.nrows); ++r) {
+                    issue(r, s);
+                    if (++s == NS) s = 0;
                 }
-                issued = r + 1;
-            };
-            for (int r = 0; r < min(NS, nrows); ++r) issue(r);
-            int k = 0;
-            for (; k < nrows; ++k) {
-                const int s = k % NS;
-                // every compute warp is done with row k (bounded; gives up at once
-                // when a compute warp has given up)
-                uint32_t spins = 0;
-                while (!ptx::mbar_try_wait(&ctl->done[s], (uint32_t)((k / NS) & 1))) {
-                    if (*(volatile int*)&ctl->abort || ++spins >= a.spin_limit) {
-                        bad = 1;
-                        break;
+                int k = 0;
+                for (; k < v.nrows; ++k) {
+                    const int s = sw;
+                    // every compute warp is done with row k (bounded; gives up at once
+                    // when a compute warp has given up)
+                    uint32_t spins = 0;
+                    while (!ptx::mbar_try_wait(&ctl->done[s], wpar)) {
+                        if (*(volatile int*)&ctl->abort || ++spins >= a.spin_limit) {
+                            bad = 1;
+                            break;
+                        }
+                    }
+                    if (bad) break;
+                    if (v.nfull > 0) {
+                        const int64_t off = (int64_t)(v.first + k * v.stride) * a.ld + 4 * (int64_t)v.f_begin;
+                        if (v.doA) ptx::bulk_s2g(a.A + off, sA(s), (uint32_t)v.nfull * 16u);
+                        if (v.doR) ptx::bulk_s2g(v.Rout + off, sR(s), (uint32_t)v.nfull * 16u);
+                    }
+                    ptx::bulk_commit();
+                    if (k + NS < v.nrows) {
+                        ptx::bulk_wait_read<0>();   // the stores no longer read stage s
+                        issue(k + NS, s);
+                    }
+                    if (++sw == NS) {
+                        sw = 0;
+                        wpar ^= 1u;
                     }
                 }
-                if (bad) break;
-                if (nfull > 0) {
-                    const int64_t off = (int64_t)(g + k * G) * a.ld + 4 * (int64_t)f_begin;
-                    if (doA) ptx::bulk_s2g(a.A + off, sA(s), (uint32_t)nfull * 16u);
-                    if (doR) ptx::bulk_s2g(Rout + off, sR(s), (uint32_t)nfull * 16u);
+                if (bad) {
+                    // drain the loads still in flight before shared memory goes away
+                    for (int j = k; j < issued; ++j) {
+                        const int q = q0 + j;
+                        ptx::mbar_wait(&ctl->full[q % NS], (uint32_t)((q / NS) & 1), a.spin_limit);
+                    }
+                    atomicExch(&v.st->error, 1);
+                    break;
                 }
-                ptx::bulk_commit();
-                if (k + NS < nrows) {
-                    ptx::bulk_wait_read<0>();   // the stores no longer read stage s
-                    issue(k + NS);
-                }
-            }
-            if (bad) {
-                // drain the loads still in flight before shared memory goes away
-                for (int q = k; q < issued; ++q)
-                    ptx::mbar_wait(&ctl->full[q % NS], (uint32_t)((q / NS) & 1), a.spin_limit);
-                atomicExch(&st->error, 1);
+                q0 += v.nrows;
             }
             ptx::bulk_wait_all();
         }
     } else {
         // ------------------------------ compute warps ------------------------------
-        float4 cv[EPT], acc[EPT];
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            cv[q] = acc[q];
-            const int f = f_begin + tid + q * T;
-            if (doA && f < f_end) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = 4 * f + e;
-                    set_lane(cv[q], e, k < a.n ? oml * a.cvec[k] : 0.f);   // (1-lambda) c(k)
-                }
-            }
-        }
         const uint32_t nslot = (uint32_t)(csize * nw);
-        // Bytes landing in this CTA's slot buffer per row: every warp of the
-        // cluster sends (m1, m2, dv, j1); the decision index dj goes to rank 0
-        // only, where warp 0 makes the row's decision.
-        const bool decide = doA && crank == 0 && wid == 0;
-        const uint32_t xbytes = nslot * (16u + ((doA && crank == 0) ? 4u : 0u));
-        uint32_t xphase = 0;                    // phase bits of xbar[0..kXBuf-1]
-        // per-row scalars are loaded a row or two ahead, off the critical path
-        float colp_next = (doA && nrows > 0) ? a.colp[g] : 0.f;
-        int ef_next = (decide && lid == 0 && nrows > 0) ? a.eflag[g] : 0;
-        int ef_prev = 0;
+        uint32_t xphase = 0;                    // phase bits of xbar[0..XB-1]
         // Software pipeline over rows (three or more stages): iteration r forms
         // row r's partial result (phase 1) and sends it, then finishes row r-1
         // (phase 2), whose partials have been in flight across the cluster
@@ -292,23 +307,52 @@ sweep_kernel(SweepLaunch L) {
         // two stages iteration r finishes row r itself, so that the producer
         // still keeps one row in flight.
         const int pipe = NS >= 3 ? 1 : 0;
-        for (int r = 0; r < nrows + pipe; ++r) {
-            int ef_this = 0;
-            if (r < nrows) {
-                const int i = g + r * G;
-                const int s = r % NS;
-                const int xb = r % kXBuf;
-                const float colp_i = colp_next;
-                if (doA && r + 1 < nrows) colp_next = a.colp[i + G];
-                ef_this = ef_next;
-                if (decide && lid == 0 && r + 1 < nrows) ef_next = a.eflag[i + G];
-                // a give-up is made warp-uniform: the warp's lanes stay converged
-                // for the redux reductions below
-                const bool ok = ptx::mbar_wait(&ctl->full[s], (uint32_t)((r / NS) & 1), a.spin_limit);
-                if (__any_sync(0xffffffffu, !ok)) {
-                    bad = 1;
-                    break;
+        int q0 = 0;                             // rows of this cluster's earlier units
+        int sg = 0;                             // stage of the next row
+        uint32_t spar = 0;                      // and the parity of its full barrier's phase
+        int x1 = 0, x2 = 0;                     // exchange buffers of the next phase-1 and phase-2 rows
+        for (int u = u_begin; u < u_end && !bad; ++u) {
+            UnitView v;
+            if (!unit_view(L, u, crank, v)) continue;
+            const SweepArgs& a = *v.a;
+            SweepState* st = v.st;
+            const int g = v.g, first = v.first, stride = v.stride;
+            const bool doA = v.doA, doR = v.doR;
+            const float lam = a.lam, oml = 1.0f - a.lam;
+            const float2 lam2 = make_float2(lam, lam), oml2 = make_float2(oml, oml),
+                         nom2 = make_float2(-oml, -oml);
+            const int f_begin = v.f_begin, f_end = v.f_end, f_full_end = v.f_full_end;
+            const int nrows = v.nrows;
+            const int n = a.n;
+            const float* colp = a.colp;
+            int32_t* eflag = a.eflag;
+            const uint32_t spin = a.spin_limit;
+            float* Rout = v.Rout;
+            int n_changes = 0, n_ex = 0;        // counted by the deciding lane
+            float4 cv[EPT], acc[EPT];
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cv[q] = acc[q];
+                const int f = f_begin + tid + q * T;
+                if (doA && f < f_end) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int k = 4 * f + e;
+                        set_lane(cv[q], e, k < n ? oml * a.cvec[k] : 0.f);   // (1-lambda) c(k)
+                    }
                 }
+            }
+            // Bytes landing in this CTA's slot buffer per row: every warp of the
+            // cluster sends (m1, m2, dv, j1); the decision index dj goes to rank 0
+            // only, where warp 0 makes the row's decision.
+            const bool decide = doA && crank == 0 && wid == 0;
+            const uint32_t xbytes = nslot * (16u + ((doA && crank == 0) ? 4u : 0u));
+            // Phase 1 of row i, held in stage s: the availability
+            // half of the previous iteration (damped in place) with the decision
+            // arg-max, and the partial top-2 of a + s, sent to every CTA of the
+            // cluster through exchange buffer xb.
+            auto phase1 = [&](int i, int s, float colp_i, int xb) {
                 const float4* S4 = sS(s);
                 const float4* R4 = sR(s);
                 float4* A4 = sA(s);
@@ -361,7 +405,7 @@ sweep_kernel(SweepLaunch L) {
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int k = 4 * f + e;
-                                if (k < a.n) {
+                                if (k < n) {
                                     const float sv = lane(s4, e), rv = lane(r4, e);
                                     float av = lane(a4, e);
                                     if (doA) {
@@ -381,7 +425,7 @@ sweep_kernel(SweepLaunch L) {
                                     float* Arow = a.A + (int64_t)i * a.ld;
 #pragma unroll
                                     for (int e = 0; e < 4; ++e)
-                                        if (4 * f + e < a.n) Arow[4 * f + e] = lane(a4, e);
+                                        if (4 * f + e < n) Arow[4 * f + e] = lane(a4, e);
                                 }
                             }
                         }
@@ -392,30 +436,22 @@ sweep_kernel(SweepLaunch L) {
                 // one included) by st.async, completing on the receiver's xbar[xb].
                 tp = top2_warp_redux(tp);
                 argmax_warp_redux(dv, dj);
-                if (tid == 0) ptx::mbar_arrive_expect_tx(&ctl->xbar[xb], xbytes);
+                if (tid == 0) ptx::mbar_arrive_expect_tx(&xbar[xb], xbytes);
                 if (lid < csize) {
                     const uint32_t at = (uint32_t)xb * nslot + crank * nw + wid;
                     const uint32_t ra = ptx::mapa(xs + at, (uint32_t)lid);
-                    const uint32_t rb = ptx::mapa(&ctl->xbar[xb], (uint32_t)lid);
+                    const uint32_t rb = ptx::mapa(&xbar[xb], (uint32_t)lid);
                     ptx::st_async_v4(ra, __float_as_uint(tp.m1), __float_as_uint(tp.m2),
                                      __float_as_uint(dv), (uint32_t)tp.j1, rb);
                     if (doA && lid == 0)            // lane 0 writes to rank 0
                         ptx::st_async_b32(ptx::mapa(xdj + at, 0u), (uint32_t)dj, rb);
                 }
-            }
-
-            if (r - pipe >= 0) {
-                // ---- second half of row rp ----
-                const int rp = r - pipe;
-                const int ef_rp = pipe ? ef_prev : ef_this;
-                const int i = g + rp * G;
-                const int s = rp % NS;
-                const int xb = rp % kXBuf;
-                const bool ok = ptx::mbar_wait(&ctl->xbar[xb], (xphase >> xb) & 1u, a.spin_limit);
-                if (__any_sync(0xffffffffu, !ok)) {
-                    bad = 1;
-                    break;
-                }
+            };
+            // Phase 2 of row i: every warp's partials (false when the wait gave
+            // up), the row's decision, and the responsibility half.
+            auto phase2 = [&](int i, int s, int ef_rp, int xb) -> bool {
+                const bool ok = ptx::mbar_wait(&xbar[xb], (uint32_t)((xphase >> xb) & 1u), spin);
+                if (__any_sync(0xffffffffu, !ok)) return false;
                 xphase ^= 1u << xb;
                 Top2 u{-INFINITY, -INFINITY, INT_MAX};
                 float uv = -INFINITY;
@@ -432,9 +468,9 @@ sweep_kernel(SweepLaunch L) {
                     if (lid == 0) {
                         if (a.dec) a.dec[i] = uj;
                         const int e = (uj == i) ? 1 : 0;
-                        if (ef_rp != e) ++ctl->cnt_changes;
-                        a.eflag[i] = e;
-                        ctl->cnt_ex += e;
+                        if (ef_rp != e) ++n_changes;
+                        eflag[i] = e;
+                        n_ex += e;
                     }
                 }
                 if (doR) {
@@ -475,7 +511,7 @@ sweep_kernel(SweepLaunch L) {
                                     const float om = (k == j1) ? om2 : om1;
                                     const float rn = fmaf(lam, rv, fmaf(oml, sv, -om));
                                     set_lane(o, e, rn);
-                                    if (k < a.n) {
+                                    if (k < n) {
                                         if (k == i) a.rkk[i] = rn;
                                         else set_lane(acc[q], e, lane(acc[q], e) + fmaxf(0.f, rn));
                                     }
@@ -486,40 +522,88 @@ sweep_kernel(SweepLaunch L) {
                                     float* Orow = Rout + (int64_t)i * a.ld;
 #pragma unroll
                                     for (int e = 0; e < 4; ++e)
-                                        if (4 * f + e < a.n) Orow[4 * f + e] = lane(o, e);
+                                        if (4 * f + e < n) Orow[4 * f + e] = lane(o, e);
                                 }
                             }
                         }
                     }
                 }
-                // hand the stage to the producer: this warp's shared-memory writes
-                // are made visible to the bulk stores, then one lane arrives
+                return true;
+            };
+            // hand stage s back to the producer: this warp's shared-memory writes
+            // are made visible to the bulk stores, then one lane arrives
+            auto release = [&](int s) {
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
                 if (lid == 0) ptx::mbar_arrive(&ctl->done[s]);
+            };
+            // per-row scalars are loaded a row ahead, off the critical path
+            float colp_next = (doA && nrows > 0) ? colp[first] : 0.f;
+            int ef_next = (decide && lid == 0 && nrows > 0) ? eflag[first] : 0;
+            int ef_prev = 0, s_prev = 0;
+            for (int r = 0; r < nrows + pipe; ++r) {
+                int ef_this = 0, s_this = 0;
+                if (r < nrows) {
+                    const int i = first + r * stride;
+                    const float colp_i = colp_next;
+                    if (doA && r + 1 < nrows) colp_next = colp[i + stride];
+                    ef_this = ef_next;
+                    if (decide && lid == 0 && r + 1 < nrows) ef_next = eflag[i + stride];
+                    // a give-up is made warp-uniform: the warp's lanes stay
+                    // converged for the redux reductions
+                    const bool ok = ptx::mbar_wait(&ctl->full[sg], spar, spin);
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        bad = 1;
+                        break;
+                    }
+                    s_this = sg;
+                    if (++sg == NS) {
+                        sg = 0;
+                        spar ^= 1u;
+                    }
+                    phase1(i, s_this, colp_i, x1);
+                    if (++x1 == XB) x1 = 0;
+                }
+                if (r - pipe >= 0) {
+                    const int rp = r - pipe;
+                    const int s = pipe ? s_prev : s_this;
+                    if (!phase2(first + rp * stride, s, pipe ? ef_prev : ef_this, x2)) {
+                        bad = 1;
+                        break;
+                    }
+                    if (++x2 == XB) x2 = 0;
+                    release(s);
+                }
+                ef_prev = ef_this;
+                s_prev = s_this;
             }
-            ef_prev = ef_this;
-        }
-        if (bad) *(volatile int*)&ctl->abort = 1;
-        if (bad) atomicExch(&st->error, 1);
-        if (doR && !bad) {
-            float* P = a.pcol + (int64_t)g * a.n;
+            if (bad) {
+                atomicExch(&st->error, 1);
+                break;
+            }
+            // the unit's column partials go to its own slot: the sums over
+            // slots are taken in a fixed order whichever cluster ran the unit
+            if (doR) {
+                float* P = a.pcol + (int64_t)g * a.pstride;
 #pragma unroll
-            for (int q = 0; q < EPT; ++q) {
-                const int f = f_begin + tid + q * T;
-                if (f < f_end) {
+                for (int q = 0; q < EPT; ++q) {
+                    const int f = f_begin + tid + q * T;
+                    if (f < f_end) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (4 * f + e < a.n) P[4 * f + e] = lane(acc[q], e);
+                        for (int e = 0; e < 4; ++e)
+                            if (4 * f + e < n) P[4 * f + e] = lane(acc[q], e);
+                    }
                 }
             }
+            if (decide && lid == 0) {
+                atomicAdd(&st->changes, n_changes);
+                atomicAdd(&st->n_ex, n_ex);
+            }
+            q0 += nrows;
         }
+        if (bad) *(volatile int*)&ctl->abort = 1;
     }
     __syncthreads();
-    if (tid == 0 && crank == 0 && doA) {
-        atomicAdd(&st->changes, ctl->cnt_changes);
-        atomicAdd(&st->n_ex, ctl->cnt_ex);
-    }
     // keep this CTA's shared memory alive until every peer is done with it
     if (csize > 1) cluster.sync();
 }
@@ -541,7 +625,7 @@ __global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const Sw
     float s = 0.f;
     if (k < a.n) {
 #pragma unroll 4
-        for (int g = gy; g < a.G; g += kFinLanes) s += a.pcol[(int64_t)g * a.n + k];
+        for (int g = gy; g < a.G; g += kFinLanes) s += a.pcol[(int64_t)g * a.pstride + k];
     }
     part[gy][cx] = s;
     __syncthreads();
@@ -603,24 +687,22 @@ __global__ void nonfinite_kernel(const SweepArgs* __restrict__ table) {
 // ---------------------------------------------------------------------------
 struct SweepConfig {
     int C, T, EPT, W4, G, NS;
+    int R;                        // resident clusters (G = min(R, n): a single problem's clusters)
     size_t smem;
 };
 
-template <int EPT>
-static void* sweep_fn() { return (void*)sweep_kernel<EPT>; }
-
 static void* sweep_ptr(int ept) {
     switch (ept) {
-        case 1: return sweep_fn<1>();
-        case 2: return sweep_fn<2>();
-        case 3: return sweep_fn<3>();
-        default: return sweep_fn<4>();
+        case 1: return (void*)sweep_kernel<1>;
+        case 2: return (void*)sweep_kernel<2>;
+        case 3: return (void*)sweep_kernel<3>;
+        default: return (void*)sweep_kernel<4>;
     }
 }
 
 static size_t sweep_smem(int w4, int ns, int C, int T) {
     const size_t slots = (size_t)kXBuf * C * (T / 32);
-    return (size_t)ns * 3 * w4 * sizeof(float4) + sizeof(Ctl) +
+    return (size_t)ns * 3 * w4 * sizeof(float4) + sizeof(Ctl) + kXBuf * sizeof(uint64_t) +
            (slots * (sizeof(Slot) + sizeof(int)) + 15) / 16 * 16;
 }
 
@@ -672,6 +754,7 @@ static int32_t make_config(int n, int C, int ept, int ns, SweepConfig* c) {
     c->W4 = w4;
     c->NS = ns;
     c->smem = smem;
+    c->R = num;
     c->G = std::max(1, std::min(num, n));
     return AP_OK;
 }
@@ -763,71 +846,151 @@ struct Problem {
 };
 
 // How a batch is launched: one configuration (chosen for the largest
-// problem) and the grid's clusters split between problems by work (n^2).
+// problem) and a work list of units spread over the launch's clusters.
 struct Plan {
     SweepConfig c;
-    std::vector<int> G;
+    std::vector<int> G;           // units of each problem (0: finished)
+    std::vector<int> ufirst;      // each problem's first column-partial slot in the pool
+    std::vector<Unit> units;      // grouped by cluster
+    std::vector<int> ubeg;        // clusters + 1
     int clusters = 0;
     int nmax = 0;
 };
 
-// The resident clusters split between the active problems by work (n^2):
-// each active problem gets at least one and at most min(n, resident);
-// finished problems get none (their rows are done).  Clusters are numbered in
-// problem order.
-static void split_clusters(const Problem* P, int count, const std::vector<char>& active,
-                           int resident, Plan* plan) {
-    double work = 0.0;
-    int nact = 0;
+// Cost of one row of n elements, in element-equivalents: n when the row is
+// bandwidth-bound, and never below the fixed cost of a row's round trip
+// through the cluster, in units of one resident cluster's share of the HBM
+// bandwidth (20 B per element).
+static double row_cost(int64_t n, const SweepConfig& c) {
+    const double t_row = 0.6e-6 * std::pow((double)c.C, 0.8);
+    const double elems = t_row * 6.5e12 / (20.0 * std::max(c.R, 1));
+    return std::max((double)n, elems);
+}
+
+// The work list for the active problems.  Laid end to end (problem order,
+// each row weighted by row_cost), the work is cut into R equal shares, one
+// per resident cluster, and every row goes to the share holding its
+// midpoint; a problem's rows in one share form one unit.  Where consecutive
+// shares hold nothing but rows of one problem (always, for a single problem)
+// their rows are dealt out to them interleaved instead -- share m of M takes
+// rows A + m, A + m + M, ... -- so that the problem's clusters move through
+// memory side by side (contiguous blocks per cluster measured about 3 %
+// slower).  A problem's units are consecutive in the list and number at most
+// min(R, n); the list has at most R + count - 1.  Shares that receive no row
+// are dropped.  The same active set always yields the same plan.
+static void plan_units(const Problem* P, int count, const std::vector<char>& active, Plan* plan) {
+    const SweepConfig& c = plan->c;
+    const int K = std::max(c.R, 1);
+    std::vector<double> rc(count, 0.0);
+    double total = 0.0;
     for (int b = 0; b < count; ++b)
         if (active[b]) {
-            work += (double)P[b].n * (double)P[b].n;
-            ++nact;
+            rc[b] = row_cost(P[b].n, c);
+            total += (double)P[b].n * rc[b];
         }
-    plan->G.assign(count, 0);
-    plan->clusters = 0;
+    const double share = std::max(total / K, 1e-30);
+    // contiguous pieces (b, first row, end row, share)
+    struct Piece { int b, r0, r1, k; };
+    std::vector<Piece> pieces;
+    double start = 0.0;                   // work before problem b
     for (int b = 0; b < count; ++b) {
         if (!active[b]) continue;
-        const int cap = std::max(1, std::min<int>(resident, (int)P[b].n));
-        int g = (nact == 1) ? cap : (int)std::lround((double)P[b].n * (double)P[b].n / work * resident);
-        g = std::max(1, std::min(g, cap));
-        plan->G[b] = g;
-        plan->clusters += g;
+        const int n = (int)P[b].n;
+        const double w = rc[b];
+        auto share_of = [&](int j) {
+            const double k = std::floor((start + (j + 0.5) * w) / share);
+            return (int)std::min<double>(std::max(k, 0.0), K - 1);
+        };
+        for (int j = 0; j < n;) {
+            const int k = share_of(j);
+            int jend = n;
+            if (k < K - 1) {
+                // the first row whose midpoint lies beyond share k
+                jend = (int)std::ceil(((k + 1) * share - start) / w - 0.5);
+                jend = std::min(std::max(jend, j + 1), n);
+                while (jend < n && share_of(jend) == k) ++jend;      // rounding guards
+                while (jend > j + 1 && share_of(jend - 1) != k) --jend;
+            }
+            pieces.push_back({b, j, jend, k});
+            j = jend;
+        }
+        start += (double)n * w;
     }
+    std::vector<int> in_share(K, 0);
+    for (const Piece& q : pieces) ++in_share[q.k];
+    plan->G.assign(count, 0);
+    plan->ufirst.assign(count, 0);
+    plan->units.clear();
+    plan->ubeg.assign(1, 0);
+    int slots = 0, klast = -1;
+    auto emit = [&](const Piece& q, const Unit& u) {
+        if (q.k != klast) {
+            if (klast >= 0) plan->ubeg.push_back((int)plan->units.size());
+            klast = q.k;
+        }
+        plan->units.push_back(u);
+    };
+    for (size_t i = 0; i < pieces.size();) {
+        const int b = pieces[i].b;
+        if (plan->G[b] == 0) plan->ufirst[b] = slots;
+        // a run of pieces of problem b alone in their shares
+        size_t j = i;
+        while (j < pieces.size() && pieces[j].b == b && in_share[pieces[j].k] == 1) ++j;
+        if (j - i >= 2) {
+            const int M = (int)(j - i), A = pieces[i].r0, len = pieces[j - 1].r1 - A;
+            for (int m = 0; m < M; ++m)
+                emit(pieces[i + m], Unit{b, plan->G[b]++, A + m, (len - m + M - 1) / M, M, {0, 0, 0}});
+            slots += M;
+            i = j;
+            continue;
+        }
+        const Piece& q = pieces[i];
+        emit(q, Unit{b, plan->G[b]++, q.r0, q.r1 - q.r0, 1, {0, 0, 0}});
+        ++slots;
+        ++i;
+    }
+    plan->ubeg.push_back((int)plan->units.size());
+    plan->clusters = (int)plan->ubeg.size() - 1;
 }
+
+// Work-list capacity: units, clusters and per-unit column partials.
+static size_t max_units(int count, const SweepConfig& c) { return (size_t)std::max(c.R, 1) + count; }
 
 static int32_t make_plan(const Problem* P, int count, const SweepConfig* forced, Plan* plan) {
     int64_t nmax = 0;
-    double work = 0.0;
-    for (int b = 0; b < count; ++b) {
-        nmax = std::max(nmax, P[b].n);
-        work += (double)P[b].n * (double)P[b].n;
-    }
+    for (int b = 0; b < count; ++b) nmax = std::max(nmax, P[b].n);
     plan->nmax = (int)nmax;
     if (forced) plan->c = *forced;
     else AP_TRY(choose_config((int)nmax, &plan->c));
-    (void)work;
     std::vector<char> active(count, 1);
-    split_clusters(P, count, active, std::max(plan->c.G, 1), plan);
+    plan_units(P, count, active, plan);
     return AP_OK;
 }
 
 struct SweepWs {
     SweepArgs* table;
+    Unit* units;
+    int* ubeg;
+    float* pool;                  // per-unit column partials, nmax floats each
     std::vector<SweepArgs> host;
 };
 
-// Workspace: the problem table, then per problem the second R buffer, the
-// per-cluster column partials, colp, c = r(k,k)+colp, r(k,k), exemplar flags
-// and the stop state.
+// Workspace: the problem table, the work list and the per-unit column
+// partials, then per problem the second R buffer, colp, c = r(k,k)+colp,
+// r(k,k), exemplar flags and the stop state.
 static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& plan, SweepWs* w) {
     Carver cv(ws);
     SweepArgs* table = cv.take<SweepArgs>(count);
+    Unit* units = cv.take<Unit>(max_units(count, plan.c));
+    int* ubeg = cv.take<int>((size_t)std::max(plan.c.R, 1) + 1);
+    float* pool = cv.take<float>(max_units(count, plan.c) * (size_t)plan.nmax);
     if (w) {
         w->table = table;
+        w->units = units;
+        w->ubeg = ubeg;
+        w->pool = pool;
         w->host.assign(count, SweepArgs{});
     }
-    int cb = 0;
     for (int b = 0; b < count; ++b) {
         const int64_t n = P[b].n, ld = P[b].ld;
         SweepArgs a{};
@@ -838,20 +1001,18 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
         a.n = (int)n;
         a.n4 = (int)((n + 3) / 4);
         a.w4 = (a.n4 + plan.c.C - 1) / plan.c.C;
-        a.cluster_begin = cb;
         a.G = plan.G[b];
+        a.pstride = plan.nmax;
+        a.pcol = pool + (size_t)plan.ufirst[b] * plan.nmax;
         a.ns = plan.c.NS;
         a.spin_limit = 1u << 20;
         a.R1 = cv.take<float>((size_t)n * ld);
-        // room for every resident cluster: the split is redone as problems finish
-        a.pcol = cv.take<float>((size_t)std::max(1, std::min<int>(std::max(plan.c.G, 1), (int)n)) * n);
         a.colp = cv.take<float>(n);
         a.cvec = cv.take<float>(n);
         a.rkk = cv.take<float>(n);
         a.eflag = cv.take<int32_t>(n);
         a.st = cv.take<SweepState>(1);
         a.dec = P[b].dec;
-        cb += a.G;
         if (w) w->host[b] = a;
     }
     return cv.used;
@@ -874,13 +1035,8 @@ static int32_t launch_sweep(const SweepConfig& c, int clusters, const SweepLaunc
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    cudaError_t e;
-    switch (c.EPT) {
-        case 1: e = cudaLaunchKernelEx(&cfg, sweep_kernel<1>, L); break;
-        case 2: e = cudaLaunchKernelEx(&cfg, sweep_kernel<2>, L); break;
-        case 3: e = cudaLaunchKernelEx(&cfg, sweep_kernel<3>, L); break;
-        default: e = cudaLaunchKernelEx(&cfg, sweep_kernel<4>, L); break;
-    }
+    void* args[] = {const_cast<SweepLaunch*>(&L)};
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, sweep_ptr(c.EPT), args);
     return e == cudaSuccess ? AP_OK : AP_ERR_CUDA;
 }
 
@@ -978,8 +1134,19 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     carve_sweep(ws, P, count, plan, &w);
     const SweepConfig& c = plan.c;
     for (auto& a : w.host) a.lam = p->damping;
-    AP_CUDA_TRY(cudaMemcpyAsync(w.table, w.host.data(), sizeof(SweepArgs) * count,
-                                cudaMemcpyHostToDevice, s));
+    // the problem table and the work list in force (re-planned as problems finish)
+    Plan cur = plan;
+    auto upload = [&]() -> int32_t {
+        AP_CUDA_TRY(cudaMemcpyAsync(w.table, w.host.data(), sizeof(SweepArgs) * count,
+                                    cudaMemcpyHostToDevice, s));
+        AP_CUDA_TRY(cudaMemcpyAsync(w.units, cur.units.data(), sizeof(Unit) * cur.units.size(),
+                                    cudaMemcpyHostToDevice, s));
+        AP_CUDA_TRY(cudaMemcpyAsync(w.ubeg, cur.ubeg.data(), sizeof(int) * cur.ubeg.size(),
+                                    cudaMemcpyHostToDevice, s));
+        // (pageable sources: each copy has taken its bytes when the call returns)
+        return AP_OK;
+    };
+    AP_TRY(upload());
     const int nmax = plan.nmax;
     const dim3 col_grid((nmax + 255) / 256, count);
     const dim3 fin_grid((nmax + kFinCols - 1) / kFinCols, count);
@@ -1014,10 +1181,7 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     const bool timed = (p->flags & AP_FLAG_TIME_SWEEP) != 0;
     EventPairs ev;
     if (timed) AP_TRY(ev.reserve(std::max(chunk, 64)));
-    // the launch plan in force: re-split between the problems still running
-    // whenever one finishes, so that no cluster idles on a finished problem
-    Plan cur = plan;
-    SweepLaunch L{w.table, count};
+    SweepLaunch L{w.table, w.units, w.ubeg, count, c.W4, c.NS};
     int64_t launched = 0;
     int32_t worked = 0;
     double sweep_ms = 0.0;
@@ -1067,16 +1231,15 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
                     changed = true;
                 }
             if (changed) {
-                split_clusters(P, count, active, std::max(c.G, 1), &cur);
-                int cb = 0;
+                // a new work list over the problems still running, so that no
+                // cluster idles on a finished one; nothing is in flight (the
+                // states were just read back)
+                plan_units(P, count, active, &cur);
                 for (int b = 0; b < count; ++b) {
-                    w.host[b].cluster_begin = cb;
                     w.host[b].G = cur.G[b];
-                    cb += cur.G[b];
+                    w.host[b].pcol = w.pool + (size_t)cur.ufirst[b] * cur.nmax;
                 }
-                // nothing is in flight (the states were just read back)
-                AP_CUDA_TRY(cudaMemcpyAsync(w.table, w.host.data(), sizeof(SweepArgs) * count,
-                                            cudaMemcpyHostToDevice, s));
+                AP_TRY(upload());
                 chunk = std::min(chunk_for(), timed ? 64 : 1 << 30);
             }
         }
@@ -1163,6 +1326,58 @@ APGB_API int32_t ap_iterate(const float* S, float* R, float* A, int64_t n, int64
     return run_batch(&q, 1, p, out, ws, ws_bytes, static_cast<cudaStream_t>(stream), plan);
 }
 
+// Size classes of a batch.  A launch configuration is sized for its widest
+// rows, and a row costs the same number of bulk copies (and about the same
+// time) however narrow it is, so narrow rows run far below the bandwidth
+// under a wide configuration (measured: 300-point rows under a 4000-point
+// configuration reach about 1 TB/s, under their own about 2.3 TB/s).  The
+// batch is therefore split by n at powers of two from 512 up, a class with
+// less work than fills the GPU for about 25 us (8e6 elements) joins the next
+// larger one, and the classes run one after another, each with its own
+// configuration and the whole GPU.  Problem order within a class is kept.
+struct SizeClass {
+    std::vector<int> idx;         // problems of the batch
+    std::vector<Problem> P;
+    Plan plan;
+    size_t ws_off = 0, ws_bytes = 0;
+};
+
+static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>* cls, size_t* total) {
+    std::map<int, std::vector<int>> by;
+    for (int b = 0; b < count; ++b) {
+        int k = 9;
+        while (k < 31 && (int64_t(1) << k) < P[b].n) ++k;
+        by[k].push_back(b);
+    }
+    cls->clear();
+    std::vector<int> carry;
+    for (auto it = by.begin(); it != by.end(); ++it) {
+        std::vector<int> idx = carry;
+        idx.insert(idx.end(), it->second.begin(), it->second.end());
+        std::sort(idx.begin(), idx.end());
+        double work = 0.0;
+        for (int b : idx) work += (double)P[b].n * (double)P[b].n;
+        if (work < 8e6 && std::next(it) != by.end()) {
+            carry = idx;
+            continue;
+        }
+        carry.clear();
+        SizeClass c;
+        c.idx = idx;
+        for (int b : idx) c.P.push_back(P[b]);
+        cls->push_back(std::move(c));
+    }
+    size_t at = 0;
+    for (SizeClass& c : *cls) {
+        AP_TRY(make_plan(c.P.data(), (int)c.P.size(), nullptr, &c.plan));
+        c.ws_off = at;
+        c.ws_bytes = carve_sweep(nullptr, c.P.data(), (int)c.P.size(), c.plan, nullptr);
+        at = align_up(at + c.ws_bytes, kAlign);
+    }
+    *total = at;
+    return AP_OK;
+}
+
 APGB_API size_t ap_iterate_batched_workspace_size(const int64_t* n, const int64_t* ld,
                                                   int32_t count) {
     if (!n || !ld || count < 1) return 0;
@@ -1172,9 +1387,10 @@ APGB_API size_t ap_iterate_batched_workspace_size(const int64_t* n, const int64_
         P[b] = Problem{nullptr, nullptr, nullptr, n[b], ld[b], nullptr};
         if (n[b] < 2 || n[b] > INT_MAX / 4 || ld[b] < n[b]) return 0;
     }
-    Plan plan;
-    if (make_plan(P.data(), count, nullptr, &plan) != AP_OK) return 0;
-    return carve_sweep(nullptr, P.data(), count, plan, nullptr);
+    std::vector<SizeClass> cls;
+    size_t total = 0;
+    if (make_classes(P.data(), count, &cls, &total) != AP_OK) return 0;
+    return total;
 }
 
 APGB_API int32_t ap_iterate_batched(const float* S, float* R, float* A, const int64_t* offsets,
@@ -1185,9 +1401,23 @@ APGB_API int32_t ap_iterate_batched(const float* S, float* R, float* A, const in
     std::vector<Problem> P;
     AP_TRY(gather_problems(S, R, A, offsets, n, ld, count, decisions, &P));
     AP_TRY(require_sm103());
-    Plan plan;
-    AP_TRY(make_plan(P.data(), count, nullptr, &plan));
-    return run_batch(P.data(), count, p, out, ws, ws_bytes, static_cast<cudaStream_t>(stream), plan);
+    std::vector<SizeClass> cls;
+    size_t total = 0;
+    AP_TRY(make_classes(P.data(), count, &cls, &total));
+    AP_TRY(check_ws(ws, ws_bytes, total));
+    int32_t worst = AP_OK;
+    std::vector<ap_result> r;
+    for (SizeClass& c : cls) {
+        r.assign(c.P.size(), ap_result{});
+        const int32_t st = run_batch(c.P.data(), (int)c.P.size(), p, r.data(),
+                                     static_cast<char*>(ws) + c.ws_off, c.ws_bytes,
+                                     static_cast<cudaStream_t>(stream), c.plan);
+        if (st < 0) return st;
+        worst = std::max(worst, st);
+        if (out)
+            for (size_t j = 0; j < c.idx.size(); ++j) out[c.idx[j]] = r[j];
+    }
+    return worst;
 }
 
 APGB_API int32_t ap_sweep_get_config(int64_t n, ap_sweep_config* out) {
