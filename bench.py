@@ -76,12 +76,13 @@ def _peaks():
 
 def _kernel_source_hash():
     """Hash of the sweep kernel's own source: the text of sweep.cu from its
-    register-ceiling struct through the end of sweep_kernel, plus the two
-    device headers it uses (host-side edits leave the counters valid)."""
+    device-side structs (state, problem table, work list) through the end of
+    sweep_kernel, plus the two device headers it uses (host-side edits leave
+    the counters valid)."""
     csrc = os.path.join(ROOT, "paper_0910_1650_gb300", "csrc")
     with open(os.path.join(csrc, "sweep.cu")) as f:
         text = f.read()
-    lo = text.index("struct SweepRegs")
+    lo = text.index("struct SweepState")
     hi = text.index("// Column sums in a fixed cluster order")
     h = hashlib.sha256(text[lo:hi].encode())
     for name in ("common.cuh", "ptx.cuh"):
