@@ -199,16 +199,20 @@ int32_t   ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
                      ap_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
- * ap_iterate_batched -- Algorithm 1 on `count` independent problems in one
- * launch per iteration (Algorithm 2 Step 2 runs the k sub-matrices this way).
- * Problem b is the n[b] x n[b] matrix at element offset offsets[b] of the
- * S, R and A arenas, leading dimension ld[b] (offsets[b] % 4 == 0, ld[b] %
- * 4 == 0, n[b] >= 2).  Every problem uses `params`; each stops on its own
- * rule.  The grid's clusters are divided between problems in proportion to
- * n[b]^2.  offsets, n, ld: host arrays.  decisions: device int32 arena of
- * sum(n) entries (problem b's after those of problems < b) or NULL.
- * out: host array of `count` results.  Synchronous.  Returns the largest
- * per-problem status (AP_NOT_CONVERGED if any problem hit max_iter).
+ * ap_iterate_batched -- Algorithm 1 on `count` independent problems
+ * (Algorithm 2 Step 2 runs the k sub-matrices this way).  Problem b is the
+ * n[b] x n[b] matrix at element offset offsets[b] of the S, R and A arenas,
+ * leading dimension ld[b] (offsets[b] % 4 == 0, ld[b] % 4 == 0, n[b] >= 2).
+ * Every problem uses `params`; each stops on its own rule.  The problems are
+ * grouped into size classes (n split at powers of two from 512; a class with
+ * little work joins the next larger one); the classes run one after another,
+ * each with one sweep launch per iteration whose clusters share the rows of
+ * the class's running problems evenly.  offsets, n, ld: host arrays.
+ * decisions: device int32 arena of sum(n) entries (problem b's after those of
+ * problems < b) or NULL.  out: host array of `count` results; with
+ * AP_FLAG_TIME_SWEEP, sweep_ms and sweep_launches are those of the problem's
+ * size class.  Synchronous.  Returns the largest per-problem status
+ * (AP_NOT_CONVERGED if any problem hit max_iter).
  * ------------------------------------------------------------------------- */
 size_t    ap_iterate_batched_workspace_size(const int64_t* n, const int64_t* ld, int32_t count);
 int32_t   ap_iterate_batched(const float* S, float* R, float* A, const int64_t* offsets,
