@@ -204,8 +204,8 @@ int32_t   ap_iterate(const float* S, float* R, float* A, int64_t n, int64_t ld,
  * n[b] x n[b] matrix at element offset offsets[b] of the S, R and A arenas,
  * leading dimension ld[b] (offsets[b] % 4 == 0, ld[b] % 4 == 0, n[b] >= 2).
  * Every problem uses `params`; each stops on its own rule.  The problems are
- * grouped into size classes (n split at powers of two from 512; a class with
- * little work joins the next larger one); the classes run one after another,
+ * grouped into size classes (n split at 512 x 2^(j/4); a class with little
+ * work joins the next larger one); the classes run one after another,
  * each with one sweep launch per iteration whose clusters share the rows of
  * the class's running problems evenly.  offsets, n, ld: host arrays.
  * decisions: device int32 arena of sum(n) entries (problem b's after those of
