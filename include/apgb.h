@@ -440,6 +440,31 @@ int32_t   ap_sweep_autotune(const float* S, float* R, float* A, int64_t n, int64
                             void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Work distribution of ap_iterate / ap_iterate_batched, for inspection.
+ * Host only: no device is touched.
+ *
+ * ap_sweep_plan -- the work list a sweep launch uses when problems of sizes
+ * n[0..count-1] are all running, with clusters of `cluster` CTAs of which
+ * `resident` fit the GPU at once.  Unit u covers rows first, first + stride,
+ * ... (count rows) of one problem and owns that problem's column-partial
+ * slot; it is written to units[5u .. 5u+4] as (problem, slot, first, count,
+ * stride).  Cluster c runs units ubeg[c] .. ubeg[c+1]-1.  units holds cap
+ * quintuples (at most resident + count - 1 are needed), ubeg resident + 1
+ * entries.  *n_units, *n_clusters: out.  AP_ERR_INVALID_ARG for sizes < 2,
+ * cluster outside {1,2,4,8,16}, resident < 1; AP_ERR_WORKSPACE if cap is too
+ * small.
+ *
+ * ap_sweep_classes -- the size class of each problem of a batch (classes
+ * are run one after another, each with its own launch configuration):
+ * class_of[b] in 0 .. classes-1, in increasing order of size.  Returns the
+ * number of classes, or AP_ERR_INVALID_ARG.
+ * ------------------------------------------------------------------------- */
+int32_t   ap_sweep_plan(const int64_t* n, int32_t count, int32_t cluster, int32_t resident,
+                        int32_t* units, int32_t cap, int32_t* ubeg, int32_t* n_units,
+                        int32_t* n_clusters);
+int32_t   ap_sweep_classes(const int64_t* n, int32_t count, int32_t* class_of);
+
+/* ---------------------------------------------------------------------------
  * ap_exemplars -- outputs of Algorithm 1 from final messages.
  * E = {k : argmax_j (a(k,j)+r(k,j)) == k} (lowest index on ties); exemplars
  * keep idx(k) = k, every other point takes the exemplar of highest s(i,k)

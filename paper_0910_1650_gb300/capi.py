@@ -158,6 +158,9 @@ _SIGNATURES = {
                                _P, _P, _P, C.POINTER(AplResult), _P, _SZ, _P]),
     "ap_sweep_get_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_set_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
+    "ap_sweep_plan": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, _P,
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ap_sweep_classes": (C.c_int32, [_P, C.c_int32, _P]),
     "ap_sweep_autotune_workspace_size": (_SZ, [_I64, _I64]),
     "ap_sweep_autotune": (C.c_int32, [_P, _P, _P, _I64, _I64, C.c_float, C.c_int32,
                                       C.POINTER(ApSweepConfig), _P, _SZ, _P]),
@@ -465,6 +468,32 @@ def ap_sweep_set_config(n, cluster=None, ept=None, stages=None):
         c = ApSweepConfig(int(cluster), int(ept), int(stages), 0, 0, 0, 0.0, 0)
         st = lib().ap_sweep_set_config(int(n), C.byref(c))
     _check("ap_sweep_set_config", st, ok=(AP_OK,))
+
+
+def ap_sweep_plan(n, cluster, resident):
+    """The sweep's work list for problems of sizes n, all running, with clusters
+    of `cluster` CTAs of which `resident` fit at once (host only).  Returns
+    (units as a list of (problem, slot, first, count, stride), ubeg list)."""
+    n_a = _i64_array(n)
+    cap = int(resident) + len(n)
+    units = (C.c_int32 * (5 * cap))()
+    ubeg = (C.c_int32 * (int(resident) + 1))()
+    nu, nc = C.c_int32(0), C.c_int32(0)
+    _check("ap_sweep_plan", lib().ap_sweep_plan(C.cast(n_a, C.c_void_p), len(n), int(cluster),
+                                                int(resident), C.cast(units, C.c_void_p), cap,
+                                                C.cast(ubeg, C.c_void_p), C.byref(nu), C.byref(nc)),
+           ok=(AP_OK,))
+    us = [tuple(units[5 * u:5 * u + 5]) for u in range(nu.value)]
+    return us, list(ubeg[:nc.value + 1])
+
+
+def ap_sweep_classes(n):
+    """The size class of every problem of a batch (host only)."""
+    n_a = _i64_array(n)
+    out = (C.c_int32 * len(n))()
+    k = lib().ap_sweep_classes(C.cast(n_a, C.c_void_p), len(n), C.cast(out, C.c_void_p))
+    _check("ap_sweep_classes", min(k, 0), ok=(AP_OK,))
+    return list(out)
 
 
 def ap_sweep_autotune(S, R=None, A=None, damping=0.9, iters=5, stream=None):

@@ -1348,7 +1348,8 @@ struct SizeClass {
     size_t ws_off = 0, ws_bytes = 0;
 };
 
-static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>* cls, size_t* total) {
+// The problems of each class, classes in increasing order of size (host only).
+static void split_classes(const Problem* P, int count, std::vector<std::vector<int>>* groups) {
     std::map<int, std::vector<int>> by;
     for (int b = 0; b < count; ++b) {
         // class boundaries at n = 512 x 2^(j / kClassesPerOctave)
@@ -1356,7 +1357,7 @@ static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>*
         const int k = P[b].n <= 512 ? 0 : (int)std::ceil(x - 1e-9);
         by[k].push_back(b);
     }
-    cls->clear();
+    groups->clear();
     std::vector<int> carry;
     for (auto it = by.begin(); it != by.end(); ++it) {
         std::vector<int> idx = carry;
@@ -1369,6 +1370,15 @@ static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>*
             continue;
         }
         carry.clear();
+        groups->push_back(idx);
+    }
+}
+
+static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>* cls, size_t* total) {
+    std::vector<std::vector<int>> groups;
+    split_classes(P, count, &groups);
+    cls->clear();
+    for (const auto& idx : groups) {
         SizeClass c;
         c.idx = idx;
         for (int b : idx) c.P.push_back(P[b]);
@@ -1383,6 +1393,56 @@ static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>*
     }
     *total = at;
     return AP_OK;
+}
+
+APGB_API int32_t ap_sweep_plan(const int64_t* n, int32_t count, int32_t cluster, int32_t resident,
+                              int32_t* units, int32_t cap, int32_t* ubeg, int32_t* n_units,
+                              int32_t* n_clusters) {
+    if (!n || count < 1 || !units || !ubeg || !n_units || !n_clusters || resident < 1 ||
+        cluster < 1 || cluster > kMaxCluster || (cluster & (cluster - 1)))
+        return AP_ERR_INVALID_ARG;
+    std::vector<Problem> P(count);
+    int64_t nmax = 0;
+    for (int b = 0; b < count; ++b) {
+        if (n[b] < 2 || n[b] > INT_MAX / 4) return AP_ERR_INVALID_ARG;
+        P[b] = Problem{nullptr, nullptr, nullptr, n[b], n[b], nullptr};
+        nmax = std::max(nmax, n[b]);
+    }
+    Plan plan;
+    plan.c = SweepConfig{};
+    plan.c.C = cluster;
+    plan.c.R = resident;
+    plan.c.G = std::max(1, (int)std::min<int64_t>(resident, nmax));
+    plan.nmax = (int)nmax;
+    plan_units(P.data(), count, std::vector<char>(count, 1), &plan);
+    if ((int64_t)plan.units.size() > cap) return AP_ERR_WORKSPACE;
+    for (size_t u = 0; u < plan.units.size(); ++u) {
+        const Unit& x = plan.units[u];
+        int32_t* o = units + 5 * u;
+        o[0] = x.b;
+        o[1] = x.g;
+        o[2] = x.first;
+        o[3] = x.count;
+        o[4] = x.stride;
+    }
+    std::copy(plan.ubeg.begin(), plan.ubeg.end(), ubeg);
+    *n_units = (int32_t)plan.units.size();
+    *n_clusters = plan.clusters;
+    return AP_OK;
+}
+
+APGB_API int32_t ap_sweep_classes(const int64_t* n, int32_t count, int32_t* class_of) {
+    if (!n || count < 1 || !class_of) return AP_ERR_INVALID_ARG;
+    std::vector<Problem> P(count);
+    for (int b = 0; b < count; ++b) {
+        if (n[b] < 2 || n[b] > INT_MAX / 4) return AP_ERR_INVALID_ARG;
+        P[b] = Problem{nullptr, nullptr, nullptr, n[b], n[b], nullptr};
+    }
+    std::vector<std::vector<int>> groups;
+    split_classes(P.data(), count, &groups);
+    for (size_t k = 0; k < groups.size(); ++k)
+        for (int b : groups[k]) class_of[b] = (int32_t)k;
+    return (int32_t)groups.size();
 }
 
 APGB_API size_t ap_iterate_batched_workspace_size(const int64_t* n, const int64_t* ld,
