@@ -142,10 +142,13 @@ int32_t   ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx,
  *           problem's own off-diagonal median; AP_PREF_SCALAR: host pref[0]
  *           for every problem; AP_PREF_VECTOR is not accepted).  No noise.
  *  pref_out host float[count] (may be NULL): the preference of each problem.
- *  The problems are spread round-robin over 4 library-owned streams (one
- *  workspace slice each, sized for the largest problem) that fork from and
- *  join back to ``stream`` by events; the stream is synchronised once, at
- *  the end.  Results equal ap_similarity on each problem bit for bit.
+ *  Each stage (column means, centring, median passes, diagonal) is one
+ *  launch for every problem of the batch on ``stream``; the Gram products
+ *  are launched per problem, round-robin over 4 library-owned streams that
+ *  fork from and join back to ``stream`` by events.  The workspace holds
+ *  every problem's scratch (its centred copy included, sized for float32).
+ *  The stream is synchronised once, at the end.  Results equal ap_similarity
+ *  on each problem bit for bit.
  *  Errors: AP_ERR_INVALID_ARG for a bad size or offset; AP_ERR_TIMEOUT as for
  *  ap_similarity.
  * ------------------------------------------------------------------------- */

