@@ -206,3 +206,38 @@ def test_batched_tiny_and_mixed_sizes_with_clusters_resplit():
                 scale = max(np.abs(ref["R"]).max(), np.abs(ref["A"]).max(), 1e-2 * np.abs(S).max())
                 assert np.abs(R - ref["R"]).max() <= TOL * scale
                 assert np.abs(A - ref["A"]).max() <= TOL * scale
+
+
+def test_batched_size_classes_match_oracle():
+    """A batch that splits into two size classes (32 problems of 520 points
+    and 8 of 1100; each class holds more than 8e6 elements of work, so
+    neither merges) runs them one after another with their own launch
+    configurations; every problem still matches the oracle after 9 fixed
+    iterations, and the converged outcome on a sample of each class."""
+    sizes = [520] * 32 + [1100] * 8
+    classes = capi.ap_sweep_classes(sizes)
+    assert classes == [0] * 32 + [1] * 8
+    mats = []
+    for j, n in enumerate(sizes):
+        X, _ = synth.gaussian_mixture(n, 8, 4 + j % 5, 700 + j, 6.0, 1.0)
+        mats.append(s32(X))
+    Sa, offs, lds = pack(mats)
+    for it, conv in ((9, 0), (1000, 15)):
+        Ra = torch.zeros_like(Sa)
+        Aa = torch.zeros_like(Sa)
+        res, _ = capi.ap_iterate_batched(Sa, Ra, Aa, offs, sizes, lds, damping=0.9, max_iter=it,
+                                         conv_iter=conv)
+        Rs, As = unpack(Ra, offs, sizes, lds), unpack(Aa, offs, sizes, lds)
+        picks = range(len(sizes)) if not conv else (0, 31, 32, 39)
+        for j in picks:
+            S, R, A, r = mats[j], Rs[j], As[j], res[j]
+            if conv:
+                ref = oap.run(S, lam=0.9, max_iter=it, convits=conv)
+                assert r["converged"] == 1
+                got = oap.exemplars(S, R, A, dtype=np.float32)
+                want = oap.exemplars(S, ref["R"], ref["A"])
+                assert np.array_equal(got["idx"], want["idx"]), j
+            else:
+                ref = oap.run(S, lam=0.9, fixed_iters=it)
+                assert r["iters"] == it
+                assert rel_inf(R, ref["R"]) <= TOL and rel_inf(A, ref["A"]) <= TOL, j
