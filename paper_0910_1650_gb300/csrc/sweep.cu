@@ -17,13 +17,15 @@
 //
 // Work layout: a thread-block cluster of C CTAs spans a row; CTA c owns a
 // fixed slice of W4 float4 columns, so the column partial sums for its slice
-// stay in registers across every row the cluster processes.  Each warp reduces
-// its share of the row's top-2 and decision arg-max (redux.sync) and pushes it
-// to every CTA of the cluster through distributed shared memory; rows are
+// stay in registers across every row of a work unit.  Each warp reduces its
+// share of the row's top-2 and decision arg-max (redux.sync) and pushes it to
+// every CTA of the cluster through distributed shared memory; rows are
 // software-pipelined so that this exchange overlaps the next row's first half.
-// Clusters stride over rows.  A second small kernel sums the per-cluster column
-// partials in a fixed order (bitwise reproducible), and updates the
-// device-side stop state.
+// Each cluster runs a host-made list of units (rows of one problem, each unit
+// with its own column-partial slot), cut so that every cluster gets an equal
+// share of the work.  A second small kernel sums each problem's unit partials
+// in a fixed order (bitwise reproducible), and updates the device-side stop
+// state.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -608,11 +610,11 @@ sweep_kernel(SweepLaunch L) {
     if (csize > 1) cluster.sync();
 }
 
-// Column sums in a fixed cluster order, then the stop rule (block 0 of each
-// problem).  Grid: (column blocks, problems).
-// Block: 32 columns x 8 lanes over the cluster partials; each lane sums every
-// 8th partial, then the 8 lane sums are added in a fixed tree, so the result
-// does not depend on the schedule.  Grid: (ceil(n/32), problems).
+// Column sums in a fixed order, then the stop rule (block 0 of each
+// problem).  Block: 32 columns x 8 lanes over the problem's G unit partials;
+// each lane sums every 8th partial, then the 8 lane sums are added in a fixed
+// tree, so the result does not depend on the schedule.
+// Grid: (ceil(n/32), problems).
 constexpr int kFinCols = 32, kFinLanes = 8;
 
 __global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const SweepArgs* __restrict__ table) {
