@@ -83,7 +83,7 @@ def _kernel_source_hash():
     with open(os.path.join(csrc, "sweep.cu")) as f:
         text = f.read()
     lo = text.index("struct SweepState")
-    hi = text.index("// Column sums in a fixed cluster order")
+    hi = text.index("// Column sums in a fixed order")
     h = hashlib.sha256(text[lo:hi].encode())
     for name in ("common.cuh", "ptx.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
