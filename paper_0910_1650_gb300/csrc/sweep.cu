@@ -974,6 +974,7 @@ struct SweepWs {
     Unit* units;
     int* ubeg;
     float* pool;                  // per-unit column partials, nmax floats each
+    SweepState* states;           // one per problem, contiguous (one read-back per check)
     std::vector<SweepArgs> host;
 };
 
@@ -986,11 +987,13 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
     Unit* units = cv.take<Unit>(max_units(count, plan.c));
     int* ubeg = cv.take<int>((size_t)std::max(plan.c.R, 1) + 1);
     float* pool = cv.take<float>(max_units(count, plan.c) * (size_t)plan.nmax);
+    SweepState* states = cv.take<SweepState>((size_t)count);
     if (w) {
         w->table = table;
         w->units = units;
         w->ubeg = ubeg;
         w->pool = pool;
+        w->states = states;
         w->host.assign(count, SweepArgs{});
     }
     for (int b = 0; b < count; ++b) {
@@ -1013,7 +1016,7 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
         a.cvec = cv.take<float>(n);
         a.rkk = cv.take<float>(n);
         a.eflag = cv.take<int32_t>(n);
-        a.st = cv.take<SweepState>(1);
+        a.st = states ? states + b : nullptr;
         a.dec = P[b].dec;
         if (w) w->host[b] = a;
     }
@@ -1158,9 +1161,8 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     AP_TRY(last_error());
     std::vector<SweepState> hs(count);
     auto read_states = [&]() -> int32_t {
-        for (int b = 0; b < count; ++b)
-            AP_CUDA_TRY(cudaMemcpyAsync(&hs[b], w.host[b].st, sizeof(SweepState),
-                                        cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.states, sizeof(SweepState) * count,
+                                    cudaMemcpyDeviceToHost, s));
         AP_CUDA_TRY(cudaStreamSynchronize(s));
         return AP_OK;
     };
