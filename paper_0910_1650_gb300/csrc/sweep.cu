@@ -309,7 +309,6 @@ sweep_kernel(SweepLaunch L) {
         // two stages iteration r finishes row r itself, so that the producer
         // still keeps one row in flight.
         const int pipe = NS >= 3 ? 1 : 0;
-        int q0 = 0;                             // rows of this cluster's earlier units
         int sg = 0;                             // stage of the next row
         uint32_t spar = 0;                      // and the parity of its full barrier's phase
         int x1 = 0, x2 = 0;                     // exchange buffers of the next phase-1 and phase-2 rows
@@ -350,10 +349,10 @@ sweep_kernel(SweepLaunch L) {
             // only, where warp 0 makes the row's decision.
             const bool decide = doA && crank == 0 && wid == 0;
             const uint32_t xbytes = nslot * (16u + ((doA && crank == 0) ? 4u : 0u));
-            // Phase 1 of row i, held in stage s: the availability
-            // half of the previous iteration (damped in place) with the decision
-            // arg-max, and the partial top-2 of a + s, sent to every CTA of the
-            // cluster through exchange buffer xb.
+            // Phase 1 of row i, held in stage s: the availability half of the
+            // previous iteration (damped in place) with the decision arg-max, and
+            // the partial top-2 of a + s, sent to every CTA of the cluster through
+            // exchange buffer xb.
             auto phase1 = [&](int i, int s, float colp_i, int xb) {
                 const float4* S4 = sS(s);
                 const float4* R4 = sR(s);
@@ -601,7 +600,6 @@ sweep_kernel(SweepLaunch L) {
                 atomicAdd(&st->changes, n_changes);
                 atomicAdd(&st->n_ex, n_ex);
             }
-            q0 += nrows;
         }
         if (bad) *(volatile int*)&ctl->abort = 1;
     }
