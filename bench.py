@@ -708,6 +708,40 @@ def similarity_only(args):
                       "ms": round(ms, 4), "tflops": round(fl / ms / 1e9, 1)}), flush=True)
 
 
+def batch_similarity(args):
+    """The batched similarity build alone on the first COUNT problems of the
+    256-problem image batch (features uploaded once, one S arena, workspace
+    allocated once): --warmup untimed calls, then --steps timed ones; prints
+    one JSON line, for profiling."""
+    import numpy as np
+    import torch
+
+    from paper_0910_1650_gb300 import batched, capi
+
+    probs = list(batched.image_batch(args.batch_similarity))
+    rows = [p.shape[0] for p in probs]
+    d = probs[0].shape[1]
+    X = torch.from_numpy(np.concatenate(probs)).cuda()
+    xoff = np.concatenate([[0], np.cumsum(rows)[:-1]]) * d
+    off, n, ld, total = batched.layout(rows)
+    S = torch.empty(total, dtype=torch.float32, device="cuda")
+    ws = capi.ap_similarity_batched_workspace(n, d, X.device)
+    for _ in range(args.warmup):
+        capi.ap_similarity_batched(X, xoff, n, S, off, ld, precision="bf16", ws=ws)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(args.steps):
+        capi.ap_similarity_batched(X, xoff, n, S, off, ld, precision="bf16", ws=ws)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    fl = sum(2.0 * m * m * d for m in rows)
+    print(json.dumps({"case": "batch_similarity", "problems": len(rows), "d": d,
+                      "sum_n2": float(sum(float(m) * m for m in rows)), "ms": round(ms, 4),
+                      "tflops": round(fl / ms / 1e9, 1)}), flush=True)
+
+
 def lap_only(args):
     """Landmark AP alone (Steps 1-2 of Algorithm 3: landmark similarity and
     AP, then the tensor-core nearest-exemplar assignment) on the first N
@@ -747,7 +781,13 @@ def main():
     ap.add_argument("--similarity-only", type=int, default=0, metavar="D",
                     help="profiling aid: time the bf16 similarity build alone on one image-like "
                          "problem of --n points and D features, print one JSON line")
+    ap.add_argument("--batch-similarity", type=int, default=0, metavar="COUNT",
+                    help="profiling aid: time the batched bf16 similarity build alone on the first "
+                         "COUNT problems of the image batch, print one JSON line")
     args = ap.parse_args()
+    if args.batch_similarity:
+        batch_similarity(args)
+        return
     if args.similarity_only:
         similarity_only(args)
         return
