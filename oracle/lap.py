@@ -1,5 +1,6 @@
-"""Landmark affinity propagation, Algorithm 3 of Xia et al. (Section 4),
-Steps 1 and 2 without the max_distance gate.
+"""Landmark affinity propagation, Algorithm 3 of Xia et al. (Section 4):
+Steps 1 and 2 without the max_distance gate (``run``), Steps 1-4
+(``run_full``) and Step 4's refinement (``refine``).
 
 TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
 
@@ -70,7 +71,8 @@ def _sqdist(A, B):
     return ((A[:, None, :] - B[None, :, :]) ** 2).sum(axis=2)
 
 
-def run_full(X, n_landmarks, seed, m0, lam=0.5, max_iter=200, convits=15, max_levels=8):
+def run_full(X, n_landmarks, seed, m0, lam=0.5, max_iter=200, convits=15, max_levels=8,
+             refine_rounds=0):
     """Algorithm 3 Steps 1-4 (Section 4), literally:
 
     Step 1  uniform landmarks (``uniform_landmarks`` with the level's seed),
@@ -83,8 +85,10 @@ def run_full(X, n_landmarks, seed, m0, lam=0.5, max_iter=200, convits=15, max_le
     Step 3  the m unassigned points: Algorithm 1 on them when m <= m0 (one
             point is its own exemplar), else Steps 1-3 on them recursively
             (seed + level); their exemplars join the set.
-    Step 4  every point is reassigned to its nearest exemplar of the merged
-            set; exemplars keep themselves.
+    Step 4  with refine_rounds > 0, the merged set is first refined by
+            ``refine`` (a local search on net similarity); then every point
+            is reassigned to its nearest exemplar of the set; exemplars keep
+            themselves.
 
     Readings: distances are squared Euclidean (the negative of s); the nearest
     exemplar and the gate are decided on the bf16-rounded centred points of
@@ -154,6 +158,9 @@ def run_full(X, n_landmarks, seed, m0, lam=0.5, max_iter=200, convits=15, max_le
     if E.size == 0:
         return dict(E=E, idx=np.full(n, -1), levels=levels, pref=p, dpsim=np.nan,
                     expref=np.nan, netsim=np.nan)
+    refine_history = []
+    if refine_rounds > 0:
+        E, refine_history = refine(X, E, p, refine_rounds)
     # Step 4: nearest exemplar of the merged set, on the whole set's rounded points
     Xr = _rounded_points(X)
     D = _sqdist(Xr, Xr[E])
@@ -167,4 +174,104 @@ def run_full(X, n_landmarks, seed, m0, lam=0.5, max_iter=200, convits=15, max_le
     dpsim = float(s_ic.sum())
     expref = float(p * E.size)
     return dict(E=E, idx=idx, levels=levels, pref=p, gap=gap4, dpsim=dpsim, expref=expref,
-                netsim=dpsim + expref)
+                netsim=dpsim + expref, refine=refine_history)
+
+
+# ---- Algorithm 3 Step 4: refinement of the merged centres ------------------------------
+
+def _top2(D):
+    """Nearest and second-nearest column of every row of the distance matrix
+    D (lowest column on ties), and those distances; the second is -1 / inf
+    when D has one column."""
+    n, c = D.shape
+    j1 = np.argmin(D, axis=1)
+    d1 = D[np.arange(n), j1]
+    if c == 1:
+        return j1, d1, np.full(n, -1), np.full(n, np.inf)
+    D2 = D.copy()
+    D2[np.arange(n), j1] = np.inf
+    j2 = np.argmin(D2, axis=1)
+    return j1, d1, j2, D2[np.arange(n), j2]
+
+
+def netsim_rounded(X, E, pref):
+    """Net similarity of the centre set E (every point at its nearest centre,
+    centres at themselves) measured on the bf16-rounded centred points: the
+    quantity the refinement's decisions are taken on."""
+    Xr = _rounded_points(X)
+    E = np.asarray(E, dtype=np.int64)
+    D = _sqdist(Xr, Xr[E])
+    d = D.min(axis=1)
+    d[E] = 0.0
+    return float(-d.sum() + pref * E.size)
+
+
+def refine(X, E, pref, max_rounds=8):
+    """Step 4 ("refine the final set of centers and classes, recalculate the
+    similarity and obtain the best final results"), read as a local search
+    on the net similarity of Section 2 (netsim = -E(c): the summed similarity
+    of every point to its centre plus the preference p < 0 of every centre).
+    One round:
+      1. every point joins its nearest centre j1 (second nearest: j2), on
+         the bf16-rounded centred points;
+      2. removal: the cost of dropping centre e is what its class would lose
+         by moving to the second choices, delta(e) = sum over the points of
+         class e of d(i, j2) - d(i, j1); e is a candidate when delta(e) < -p
+         (dropping it raises netsim).  Two candidates conflict when a point
+         has one as j1 and the other as j2; of a conflicting pair only the
+         one of smaller (delta, index) may go, so the dropped centres form an
+         independent set and every member of a dropped class moves to a
+         centre that stays.  Candidates no conflict blocks are dropped;
+      3. every class (after the moves of 2) moves its centre to the member
+         nearest the class mean: sum_i |x_i - x_k|^2 over the class equals
+         n |x_k - mean|^2 plus a constant, so that member minimises the
+         class's summed squared distance (unrounded points, float64; lowest
+         index on ties).
+    Rounds repeat until one changes nothing, or max_rounds have run.
+    Returns (E sorted, list of per-round dicts: removed, moved, netsim of the
+    round's input set on the rounded points, medoid_gap: the smallest
+    relative margin by which a class's medoid beat its runner-up)."""
+    X = np.asarray(X, dtype=np.float32)
+    X64 = X.astype(np.float64)
+    Xr = _rounded_points(X)
+    E = np.unique(np.asarray(E, dtype=np.int64))
+    history = []
+    for _ in range(max_rounds):
+        D = _sqdist(Xr, Xr[E])
+        j1, d1, j2, d2 = _top2(D)
+        c = E.size
+        delta = np.zeros(c)
+        np.add.at(delta, j1, d2 - d1)                   # inf when there is no second centre
+        cand = delta < -pref
+        key = list(zip(delta.tolist(), E.tolist()))
+        blocked = np.zeros(c, dtype=bool)
+        both = (j2 >= 0)
+        for a, b in zip(j1[both], j2[both]):
+            if cand[a] and cand[b]:
+                blocked[max(a, b, key=lambda t: key[t])] = True
+        removed = cand & ~blocked
+        cls = np.where(removed[j1], j2, j1)              # class position of every point
+        newE = []
+        moved = 0
+        gap = np.inf                                     # how clear the medoid choices were
+        for j in np.nonzero(~removed)[0]:
+            members = np.nonzero(cls == j)[0]
+            if members.size == 0:
+                continue                                 # a class left empty drops its centre
+            mu = X64[members].mean(axis=0)
+            dm = ((X64[members] - mu) ** 2).sum(axis=1)
+            k = int(members[np.argmin(dm)])             # first minimum: lowest point index
+            if members.size > 1:
+                s2 = np.partition(dm, 1)[:2]
+                gap = min(gap, float(s2[1] - s2[0]) / max(1.0, float(s2[1])))
+            moved += int(k != E[j])
+            newE.append(k)
+        is_c = np.zeros(X.shape[0], dtype=bool)
+        is_c[E] = True
+        history.append(dict(removed=int(removed.sum()), moved=moved,
+                            netsim=float(-d1[~is_c].sum() + pref * c), medoid_gap=gap))
+        newE = np.unique(np.asarray(newE, dtype=np.int64))
+        if removed.sum() == 0 and moved == 0:
+            break
+        E = newE
+    return E, history

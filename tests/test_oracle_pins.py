@@ -579,3 +579,108 @@ def test_pap_carry_r_single_block_continues_the_run():
     # without carrying R the paper's Step 4 restarts R from 0 and does not continue the run
     one = pap.run(S, [0, n], lam=0.7, fixed_iters=t)
     assert not np.allclose(one["final"]["R"], straight["R"], rtol=0, atol=1e-6 * np.abs(S).max())
+
+
+# ---- Algorithm 3 Step 4: the refinement (local search on net similarity) -----------------
+
+def _integer_points(n_half, seed, spread=20):
+    """Integer points symmetric about the origin: their column mean is exactly
+    zero and every coordinate is exact in bf16, so the refinement's rounded
+    distances are the exact squared distances."""
+    g = np.random.default_rng(seed)
+    P = g.integers(-spread, spread + 1, size=(n_half, 2)).astype(np.float32)
+    return np.vstack([P, -P])
+
+
+def _netsim_exact(X, E, p):
+    X = X.astype(np.float64)
+    D = ((X[:, None, :] - X[None, E, :]) ** 2).sum(axis=2)
+    d = D.min(axis=1)
+    d[E] = 0.0
+    return -d.sum() + p * len(E)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_refine_reaches_a_brute_force_local_optimum(seed):
+    """At convergence no single centre's removal raises netsim (checked by
+    recomputing netsim without it) and every centre minimises its class's
+    summed squared distance over the class's members (checked by direct
+    sums, not through the class mean); netsim never falls from round to
+    round."""
+    X = _integer_points(20, seed)
+    n = X.shape[0]
+    g = np.random.default_rng(100 + seed)
+    E0 = np.sort(g.choice(n, 12, replace=False))
+    p = -150.0
+    E, hist = lap.refine(X, E0, p, max_rounds=100)
+    assert hist[-1]["removed"] == 0 and hist[-1]["moved"] == 0          # converged
+    ns = [h["netsim"] for h in hist]
+    assert all(b >= a - 1e-9 for a, b in zip(ns, ns[1:]))
+    assert ns[-1] == pytest.approx(_netsim_exact(X, E, p), abs=1e-9)
+    base = _netsim_exact(X, E, p)
+    for e in E:
+        rest = E[E != e]
+        if rest.size:
+            assert _netsim_exact(X, rest, p) <= base + 1e-9
+    X64 = X.astype(np.float64)
+    D = ((X64[:, None, :] - X64[None, E, :]) ** 2).sum(axis=2)
+    cls = D.argmin(axis=1)
+    for j, e in enumerate(E):
+        members = np.nonzero(cls == j)[0]
+        sums = [((X64[members] - X64[k]) ** 2).sum() for k in members]
+        best = members[int(np.argmin(sums))]
+        assert e == best
+
+
+def test_refine_drops_a_duplicate_centre_and_keeps_separated_ones():
+    """Four far clusters (mirrored pairs, for an exact zero mean), one centre
+    each plus a second centre in the first: the duplicate goes (merging its
+    class costs far less than -p), every cluster keeps one centre."""
+    g = np.random.default_rng(5)
+    A = np.round(g.normal(size=(30, 2)) * 2) + np.array([50.0, 0.0])
+    B = np.round(g.normal(size=(30, 2)) * 2) + np.array([0.0, 100.0])
+    X = np.vstack([A, B, -A, -B]).astype(np.float32)
+    E0 = np.array([0, 1, 30, 60, 90])
+    E, hist = lap.refine(X, E0, -400.0, max_rounds=20)
+    assert E.size == 4
+    assert [int(((E >= 30 * q) & (E < 30 * q + 30)).sum()) for q in range(4)] == [1, 1, 1, 1]
+    assert hist[0]["removed"] == 1
+
+
+def test_refine_conflicting_candidates_drop_only_one():
+    """Two centres of one tight group, each the other's members' second
+    choice, both cheap to drop (the same for a mirrored group): dropping both
+    would send the group to a far centre.  Only one of each pair goes, and
+    netsim rises."""
+    half = np.array([[20, 20], [21, 20], [20, 21], [21, 21], [60, -60], [61, -60]], dtype=np.float32)
+    X = np.vstack([half, -half])
+    E0 = np.array([0, 3, 4, 6, 9, 10])
+    p = -30.0
+    E, hist = lap.refine(X, E0, p, max_rounds=20)
+    assert hist[0]["removed"] == 2
+    assert ((E < 4).sum(), ((E >= 6) & (E < 10)).sum()) == (1, 1)
+    assert _netsim_exact(X, E, p) > _netsim_exact(X, E0, p)
+
+
+def test_refine_moves_a_centre_to_its_class_medoid():
+    """One class on a line, x = 0, 1, 2, 3, 10 (mirrored for a zero mean, the
+    mirror a second class): the mean is 3.2, so the member nearest it, 3, is
+    the centre that minimises the class's summed squared distance."""
+    xs = np.array([0, 1, 2, 3, 10], dtype=np.float32) + 200.0
+    X = np.zeros((10, 2), dtype=np.float32)
+    X[:5, 0] = xs
+    X[5:, 0] = -xs
+    E, hist = lap.refine(X, np.array([4, 9]), -10.0, max_rounds=10)
+    assert list(E) == [3, 8]
+    assert hist[0]["moved"] == 2 and hist[0]["removed"] == 0
+
+
+def test_lap_full_refinement_does_not_lower_netsim():
+    """Steps 1-4 with the refinement against Steps 1-4 with reassignment
+    only, on a mixture whose Step 3 adds exemplars inside existing classes:
+    at least as good a net similarity with no more exemplars."""
+    X, _ = synth.gaussian_mixture(600, 8, 6, 4242, 6.0, 1.0)
+    plain = lap.run_full(X, 80, 3, 400, lam=0.9, max_iter=1000, convits=15)
+    ref = lap.run_full(X, 80, 3, 400, lam=0.9, max_iter=1000, convits=15, refine_rounds=8)
+    assert ref["E"].size <= plain["E"].size
+    assert ref["netsim"] >= plain["netsim"] - 1e-6 * abs(plain["netsim"])
