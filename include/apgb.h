@@ -45,7 +45,10 @@ extern "C" {
 #define AP_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up       */
 #define AP_ERR_NONFINITE     -5   /* S holds NaN or +-Inf                     */
 #define AP_ERR_UNSUPPORTED   -6   /* e.g. the GPU is not sm_103               */
-#define AP_ERR_TOO_LARGE     -7   /* n exceeds a fixed built-in scratch area  */
+#define AP_ERR_TOO_LARGE     -7   /* n exceeds the fixed built-in scratch of a
+                                     no-allocation entry                      */
+#define AP_ERR_CAPACITY      -8   /* a result outgrew the capacity its
+                                     workspace was sized for                  */
 
 /* ---- options --------------------------------------------------------------- */
 #define AP_PREC_FP32   0   /* similarity by a float32 SIMT GEMM                  */
@@ -291,6 +294,26 @@ int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_l
                   void* stream);
 
 /* ---------------------------------------------------------------------------
+ * lap_assign -- Algorithm 3 (Section 4) Step 2 on its own: every point joins
+ * its nearest centre, for a given set of centres (no max_distance gate).
+ *  X        device float32 [n x ldx], the points.
+ *  centres  device int32 [c], distinct point indices of the centres (in any
+ *           order; "lowest index" on ties means lowest position in this list).
+ *  idx      device int32 [n] out: centres[argmin_j |x_i - x_centres[j]|^2],
+ *           computed as argmax_j (2 x_i.e_j - |e_j|^2) by the bf16 tensor-core
+ *           GEMM of the mean-centred features with fp32 accumulation (the
+ *           arg-max fused into its epilogue, the n x c scores never written);
+ *           centres keep themselves.
+ *  best     device float [n] out or NULL: that maximum score, on the centred
+ *           bf16-rounded features (|x_i|^2 - best is the squared distance).
+ *  ws       lap_assign_workspace_size(n, d, c) bytes.  Synchronous.
+ * ------------------------------------------------------------------------- */
+size_t    lap_assign_workspace_size(int64_t n, int64_t d, int64_t c);
+int32_t   lap_assign(const float* X, int64_t n, int64_t d, int64_t ldx, const int32_t* centres,
+                     int64_t c, int32_t* idx, float* best, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* ---------------------------------------------------------------------------
  * lap_run_full -- Algorithm 3 (Section 4), Steps 1-4:
  *  Step 1  L uniform landmarks (the L points with the smallest splitmix64 keys
  *          of seed + level, ties by index), Algorithm 1 on their S; the
@@ -305,16 +328,32 @@ int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_l
  *          its own exemplar); else Steps 1-3 on them (the next level, up to
  *          max_levels levels; points still left after the last level join
  *          their nearest exemplar in Step 4).  Exemplars of every level merge.
- *  Step 4  every point joins its nearest exemplar of the merged set
- *          (refinement by reassignment); exemplars keep themselves.
+ *  Step 4  "refine the final set of centers and classes, recalculate the
+ *          similarity and obtain the best final results", read as a local
+ *          search on net similarity (-E(c), Section 2) over the merged set,
+ *          for up to refine_rounds rounds (0: reassignment only).  A round:
+ *            a. every point's nearest and second-nearest centre (the
+ *               assignment GEMM with a top-2 epilogue);
+ *            b. the cost of dropping centre e, delta(e) = sum over its class
+ *               of d(i, second) - d(i, nearest); e is a candidate when
+ *               delta(e) < -p.  Candidates that are one point's nearest and
+ *               second-nearest conflict; of such a pair only the one of
+ *               smaller (delta, index) may go.  The unblocked candidates are
+ *               dropped and their members move to their second centre;
+ *            c. every class moves its centre to the member nearest the class
+ *               mean (unrounded features, float64), which minimises the
+ *               class's summed squared distance;
+ *          until a round changes nothing.  Sums are fixed point, so the
+ *          result is bitwise reproducible.  Then every point joins its
+ *          nearest exemplar of the final set; exemplars keep themselves.
  *  X          device float32 [n x ldx]; n_landmarks (L) in [2, n]; m0 in
- *             [2, n]; max_levels in [1, AP_LAP_MAX_LEVELS].
+ *             [2, n]; max_levels in [1, AP_LAP_MAX_LEVELS]; refine_rounds >= 0.
  *  idx        device int32[n] out: each point's exemplar.
  *  level_of   device int32[n] out (may be NULL): the level whose Step 2 (or
  *             Step 3's Algorithm 1) settled the point, -1 if none did.
  *  out        host lap_full_result*.  The call synchronises ``stream``.
  *  Errors: AP_NO_EXEMPLARS when the first level's landmarks give none (idx
- *  = -1); AP_ERR_TOO_LARGE if the merged set outgrows min(n, L*max_levels+m0).
+ *  = -1); AP_ERR_CAPACITY if the merged set outgrows min(n, L*max_levels+m0).
  * ------------------------------------------------------------------------- */
 #define AP_LAP_MAX_LEVELS 8
 typedef struct lap_full_result {
@@ -326,13 +365,44 @@ typedef struct lap_full_result {
     int32_t exemplars_at[AP_LAP_MAX_LEVELS + 1];
     float   ms;                              /* device time of the call          */
     double  dpsim, expref, netsim;
+    int32_t refine_rounds;                   /* refinement rounds run            */
+    int32_t refine_removed;                  /* centres dropped over all rounds  */
+    int32_t refine_moved;                    /* centres moved to a class medoid  */
+    int32_t pad2;
 } lap_full_result;
 size_t    lap_run_full_workspace_size(int64_t n, int64_t d, int64_t n_landmarks, int64_t m0,
                                       int32_t max_levels);
 int32_t   lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_landmarks,
                        int64_t m0, uint64_t seed, int32_t precision, const ap_params* params,
-                       int32_t max_levels, int32_t* idx, int32_t* level_of,
+                       int32_t max_levels, int32_t refine_rounds, int32_t* idx, int32_t* level_of,
                        lap_full_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * lap_refine -- Algorithm 3 (Section 4) Step 4 on its own: the refinement
+ * lap_run_full applies to its merged centres (see there), on a given centre
+ * set, for up to `rounds` rounds (0: none), followed by the reassignment of
+ * every point to its nearest centre of the final set.
+ *  X            device float32 [n x ldx].
+ *  centres      device int32 [c]: distinct point indices (any order).
+ *  pref         the preference p (< 0 for a meaningful refinement) that
+ *               every centre costs in net similarity.
+ *  centres_out  device int32 [c] out: the refined set, ascending, in its
+ *               first out->n_exemplars entries.
+ *  idx          device int32 [n] out: each point's centre.
+ *  out          host lap_refine_result*: rounds run, centres dropped and
+ *               moved, and dpsim / expref / netsim over all n points
+ *               (float64, unrounded features).
+ *  ws           lap_refine_workspace_size(n, d, c) bytes.  Synchronous.
+ *  AP_ERR_INVALID_ARG for a repeated or out-of-range centre.
+ * ------------------------------------------------------------------------- */
+typedef struct lap_refine_result {
+    int32_t rounds, removed, moved, n_exemplars;
+    double  dpsim, expref, netsim;
+} lap_refine_result;
+size_t    lap_refine_workspace_size(int64_t n, int64_t d, int64_t c);
+int32_t   lap_refine(const float* X, int64_t n, int64_t d, int64_t ldx, const int32_t* centres,
+                     int64_t c, float pref, int32_t rounds, int32_t* centres_out, int32_t* idx,
+                     lap_refine_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start.  The paper has no learned part: this network plays the
@@ -496,9 +566,15 @@ int32_t   ap_exemplars(const float* S, const float* R, const float* A,
  * accepts n <= AP_NOALLOC_MAX_N and returns AP_ERR_TOO_LARGE otherwise.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.  The caller
  * still passes S, R, A, idx and out.
- *  - The first call on each device looks up the array's device address
- *    (with that device current) and caches it; make that first call before
- *    any stream capture.
+ *  - The first call on each device does the set-up: with that device current
+ *    it looks up the array's device address (cudaGetSymbolAddress) and keeps
+ *    it for every later call on the device.  Make that first call before any
+ *    stream capture begins.  The kept address is never looked up again, so
+ *    it does not survive cudaDeviceReset or any other teardown of the
+ *    device's primary context: do not call this entry after one in the same
+ *    process.
+ *  - Like ap_exemplars it fills the host struct `out`, so it returns only
+ *    after `stream` has finished the call's work.
  *  - Every call shares the one array, which keeps the previous call's
  *    contents; nothing in it needs to start at zero (every scratch word is
  *    written before it is read).  Calls whose GPU work overlaps (different

@@ -27,6 +27,7 @@ AP_FLAG_NO_GRAPH = 2
 AP_FLAG_PAP_CARRY_R = 4
 AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
+AP_ERR_CAPACITY = -8
 AP_ERR_TIMEOUT = -4
 AP_NOALLOC_MAX_N = 65536
 
@@ -86,13 +87,24 @@ class LapFullResult(C.Structure):
     _fields_ = [("levels", C.c_int32), ("n_exemplars", C.c_int32), ("pref", C.c_float),
                 ("base_case", C.c_int32), ("unassigned", C.c_int32 * AP_LAP_MAX_LEVELS),
                 ("exemplars_at", C.c_int32 * (AP_LAP_MAX_LEVELS + 1)), ("ms", C.c_float),
-                ("dpsim", C.c_double), ("expref", C.c_double), ("netsim", C.c_double)]
+                ("dpsim", C.c_double), ("expref", C.c_double), ("netsim", C.c_double),
+                ("refine_rounds", C.c_int32), ("refine_removed", C.c_int32),
+                ("refine_moved", C.c_int32), ("pad2", C.c_int32)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad2"}
         d["unassigned"] = list(self.unassigned)[:max(self.levels, 1)]
         d["exemplars_at"] = list(self.exemplars_at)[:self.levels + self.base_case]
         return d
+
+
+class LapRefineResult(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("removed", C.c_int32), ("moved", C.c_int32),
+                ("n_exemplars", C.c_int32), ("dpsim", C.c_double), ("expref", C.c_double),
+                ("netsim", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class AplResult(C.Structure):
@@ -139,9 +151,15 @@ _SIGNATURES = {
     "lap_run_workspace_size": (_SZ, [_I64, _I64, _I64]),
     "lap_run": (C.c_int32, [_P, _I64, _I64, _I64, _I64, C.c_int32, _P, _P, C.c_uint64, C.c_int32,
                             C.POINTER(ApParams), _P, _P, C.POINTER(LapResult), _P, _SZ, _P]),
+    "lap_assign_workspace_size": (_SZ, [_I64, _I64, _I64]),
+    "lap_assign": (C.c_int32, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _P, _SZ, _P]),
+    "lap_refine_workspace_size": (_SZ, [_I64, _I64, _I64]),
+    "lap_refine": (C.c_int32, [_P, _I64, _I64, _I64, _P, _I64, C.c_float, C.c_int32, _P, _P,
+                               C.POINTER(LapRefineResult), _P, _SZ, _P]),
     "lap_run_full_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, C.c_int32]),
     "lap_run_full": (C.c_int32, [_P, _I64, _I64, _I64, _I64, _I64, C.c_uint64, C.c_int32,
-                                 C.POINTER(ApParams), C.c_int32, _P, _P, C.POINTER(LapFullResult),
+                                 C.POINTER(ApParams), C.c_int32, C.c_int32, _P, _P,
+                                 C.POINTER(LapFullResult),
                                  _P, _SZ, _P]),
     "apl_param_count": (C.c_int64, []),
     "apl_features_workspace_size": (_SZ, [_I64]),
@@ -446,10 +464,46 @@ def lap_run(X, n_landmarks, mode="uniform", score=None, landmarks=None, seed=0, 
     return idx, lm, res.as_dict()
 
 
+def lap_assign(X, centres, best=False, stream=None):
+    """Algorithm 3 Step 2 alone: every point's nearest centre (point indices
+    ``centres``).  Returns idx (int32, n) and, with ``best``, the maximum
+    score 2 x.e - |e|^2 of every point on the centred bf16 features."""
+    _dev_f32(X, "X")
+    n, d = X.shape
+    cen = centres.to(device=X.device, dtype=torch.int32).contiguous()
+    c = cen.numel()
+    idx = torch.empty(n, dtype=torch.int32, device=X.device)
+    bst = torch.empty(n, dtype=torch.float32, device=X.device) if best else None
+    ws = workspace(lib().lap_assign_workspace_size(n, d, c), X.device)
+    st = lib().lap_assign(_ptr(X), n, d, X.stride(0), _ptr(cen), c, _ptr(idx), _ptr(bst), _ptr(ws),
+                          ws.numel(), _stream(stream))
+    _check("lap_assign", st)
+    return (idx, bst) if best else idx
+
+
+def lap_refine(X, centres, pref, rounds=8, stream=None):
+    """Algorithm 3 Step 4 alone on the centre set ``centres`` (point
+    indices): returns (refined centres, ascending; idx; result dict)."""
+    _dev_f32(X, "X")
+    n, d = X.shape
+    cen = centres.to(device=X.device, dtype=torch.int32).contiguous()
+    c = cen.numel()
+    cout = torch.empty(c, dtype=torch.int32, device=X.device)
+    idx = torch.empty(n, dtype=torch.int32, device=X.device)
+    res = LapRefineResult()
+    ws = workspace(lib().lap_refine_workspace_size(n, d, c), X.device)
+    st = lib().lap_refine(_ptr(X), n, d, X.stride(0), _ptr(cen), c, float(pref), int(rounds), _ptr(cout),
+                          _ptr(idx), C.byref(res), _ptr(ws), ws.numel(), _stream(stream))
+    _check("lap_refine", st)
+    return cout[:res.n_exemplars], idx, res.as_dict()
+
+
 def lap_run_full(X, n_landmarks, m0, seed=0, precision="fp32", damping=0.5, max_iter=200,
-                 conv_iter=15, max_levels=AP_LAP_MAX_LEVELS, check_every=0, stream=None):
-    """Algorithm 3 Steps 1-4 on features X (n x d).  Returns (idx, level_of,
-    result dict)."""
+                 conv_iter=15, max_levels=AP_LAP_MAX_LEVELS, refine_rounds=0, check_every=0,
+                 stream=None):
+    """Algorithm 3 Steps 1-4 on features X (n x d); ``refine_rounds`` > 0
+    refines the merged centres in Step 4.  Returns (idx, level_of, result
+    dict)."""
     _dev_f32(X, "X")
     n, d = X.shape
     idx = torch.empty(n, dtype=torch.int32, device=X.device)
@@ -460,7 +514,8 @@ def lap_run_full(X, n_landmarks, m0, seed=0, precision="fp32", damping=0.5, max_
                    X.device)
     prec = {"fp32": AP_PREC_FP32, "bf16": AP_PREC_BF16}[precision]
     st = lib().lap_run_full(_ptr(X), n, d, X.stride(0), int(n_landmarks), int(m0),
-                            int(seed) & 0xFFFFFFFFFFFFFFFF, prec, C.byref(p), int(max_levels), _ptr(idx),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, prec, C.byref(p), int(max_levels),
+                            int(refine_rounds), _ptr(idx),
                             _ptr(level_of), C.byref(res), _ptr(ws), ws.numel(), _stream(stream))
     _check("lap_run_full", st)
     return idx, level_of, res.as_dict()

@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <climits>
 #include <vector>
 
@@ -23,6 +25,9 @@ size_t exemplars_ws_bytes(int64_t n);
 int32_t tc_assign_argmax(const __nv_bfloat16* A, int na, const __nv_bfloat16* B, int nb,
                          const float* bnrm, int dpad, int32_t* arg, float* best, int32_t* err,
                          cudaStream_t s);
+int32_t tc_assign_top2(const __nv_bfloat16* A, int na, const __nv_bfloat16* B, int nb,
+                       const float* bnrm, int dpad, int32_t* arg, float* best, int32_t* arg2,
+                       float* best2, int32_t* err, cudaStream_t s);
 
 // ---- landmark keys and exact selection of the L smallest -------------------------
 __global__ void keys_uniform_kernel(uint64_t seed, int64_t n, uint64_t* keys) {
@@ -368,6 +373,134 @@ __global__ void fill_i32_kernel(int32_t* p, int64_t n, int32_t v) {
         p[i] = v;
 }
 
+// ---- Step 4's refinement: a local search on net similarity -------------------------------
+// Removal costs are summed in fixed point (units of 2^-20), class sums of the
+// features in 64-bit fixed point (units of 2^-scale), so every sum is exact
+// integer arithmetic whatever order the atomics land in: the refinement is
+// bitwise reproducible.
+constexpr double kDeltaUnit = 1048576.0;   // 2^20
+
+// Largest |x| over the n x d features (float bits of non-negative values
+// order like unsigned integers).
+__global__ void absmax_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ldx, unsigned* out) {
+    unsigned m = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * d;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / d;
+        const int j = (int)(t - i * d);
+        m = max(m, __float_as_uint(fabsf(X[i * ldx + j])));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// delta[j1(i)] += d(i, j2) - d(i, j1) = score1 - score2 (scores 2x.e - |e|^2
+// of the rounded centred points); a class with a point that has no second
+// centre (one centre in all) can never be dropped.
+__global__ void refine_costs_kernel(int64_t n, const int32_t* __restrict__ j1, const float* __restrict__ s1,
+                                    const int32_t* __restrict__ j2, const float* __restrict__ s2,
+                                    unsigned long long* delta, int32_t* nosecond) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = j1[i];
+        if (j2[i] < 0) {
+            nosecond[a] = 1;
+            continue;
+        }
+        const double diff = (double)s1[i] - (double)s2[i];
+        atomicAdd(&delta[a], (unsigned long long)llrint(diff * kDeltaUnit));
+    }
+}
+
+// cand[j]: dropping centre j raises netsim (its removal cost is below -p).
+__global__ void refine_candidates_kernel(int c, const unsigned long long* __restrict__ delta,
+                                         const int32_t* __restrict__ nosecond, double thr, int32_t* cand) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < c) cand[j] = (!nosecond[j] && (double)delta[j] < thr) ? 1 : 0;
+}
+
+// Two candidates conflict when a point has one as nearest and the other as
+// second-nearest centre; the one of larger (cost, position) is kept.
+__global__ void refine_block_kernel(int64_t n, const int32_t* __restrict__ j1, const int32_t* __restrict__ j2,
+                                    const int32_t* __restrict__ cand,
+                                    const unsigned long long* __restrict__ delta, int32_t* blocked) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = j1[i], b = j2[i];
+        if (b < 0 || !cand[a] || !cand[b]) continue;
+        const bool a_larger = delta[a] > delta[b] || (delta[a] == delta[b] && a > b);
+        blocked[a_larger ? a : b] = 1;
+    }
+}
+
+// Class of every point once the unblocked candidates are dropped: the
+// members of a dropped class move to their second-nearest centre (which,
+// the dropped set being independent, stays).
+__global__ void refine_classes_kernel(int64_t n, const int32_t* __restrict__ j1, const int32_t* __restrict__ j2,
+                                      const int32_t* __restrict__ cand, const int32_t* __restrict__ blocked,
+                                      int32_t* cls, int32_t* counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = j1[i];
+        const int k = (cand[a] && !blocked[a]) ? j2[i] : a;
+        cls[i] = k;
+        atomicAdd(&counts[k], 1);
+    }
+}
+
+// sums[cls(i)] += x_i in fixed point (one warp per point).
+__global__ void class_sum_kernel(const float* __restrict__ X, int64_t ldx, int d, int64_t n,
+                                 const int32_t* __restrict__ cls, double scale, unsigned long long* sums) {
+    const int warps = blockDim.x >> 5, lid = threadIdx.x & 31;
+    for (int64_t i = blockIdx.x * (int64_t)warps + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * warps) {
+        unsigned long long* row = sums + (int64_t)cls[i] * d;
+        for (int j = lid; j < d; j += 32)
+            atomicAdd(row + j, (unsigned long long)llrint((double)X[i * ldx + j] * scale));
+    }
+}
+
+__global__ void class_mean_kernel(int c, int d, const unsigned long long* __restrict__ sums,
+                                  const int32_t* __restrict__ counts, double inv_scale, double* mu) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)c * d;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / d);
+        mu[t] = counts[j] ? (double)(long long)sums[t] * inv_scale / (double)counts[j] : 0.0;
+    }
+}
+
+// dist[i] = |x_i - mean of its class|^2 in float64 (one warp per point, a
+// fixed butterfly); mind[class] = the smallest, as float64 bits.
+__global__ void class_dist_kernel(const float* __restrict__ X, int64_t ldx, int d, int64_t n,
+                                  const int32_t* __restrict__ cls, const double* __restrict__ mu, double* dist,
+                                  unsigned long long* mind) {
+    const int warps = blockDim.x >> 5, lid = threadIdx.x & 31;
+    for (int64_t i = blockIdx.x * (int64_t)warps + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * warps) {
+        const int k = cls[i];
+        const double* m = mu + (int64_t)k * d;
+        double s = 0.0;
+        for (int j = lid; j < d; j += 32) {
+            const double t = (double)X[i * ldx + j] - m[j];
+            s += t * t;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lid == 0) {
+            dist[i] = s;
+            atomicMin(&mind[k], (unsigned long long)__double_as_longlong(s));
+        }
+    }
+}
+
+// medoid[class] = the lowest point index attaining the class's smallest distance.
+__global__ void class_argmin_kernel(int64_t n, const int32_t* __restrict__ cls, const double* __restrict__ dist,
+                                    const unsigned long long* __restrict__ mind, int32_t* medoid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = cls[i];
+        if ((unsigned long long)__double_as_longlong(dist[i]) == mind[k]) atomicMin(&medoid[k], (int32_t)i);
+    }
+}
+
 // ---- workspace ------------------------------------------------------------------------
 struct LapWs {
     uint64_t* keys;
@@ -571,6 +704,74 @@ APGB_API int32_t lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int6
     return (params->conv_iter > 0 && !lc) ? AP_NOT_CONVERGED : AP_OK;
 }
 
+// ---- Algorithm 3 Step 2 alone: nearest centre of every point --------------------------
+namespace apgb {
+
+struct AssignWs {
+    double* part;
+    float* mean;
+    __nv_bfloat16* Xb;
+    __nv_bfloat16* Eb;
+    float* enrm;
+    int32_t* arg;
+    int32_t* err;
+};
+
+static size_t carve_assign(void* ws, int64_t n, int64_t d, int64_t c, AssignWs* w) {
+    const int dpad = (int)((d + 63) / 64 * 64);
+    const int64_t npad = (n + 127) / 128 * 128;
+    const int64_t cpad = (c + 255) / 256 * 256;
+    Carver cv(ws);
+    w->part = cv.take<double>(column_mean_part_doubles(n, (int)d));
+    w->mean = cv.take<float>(d);
+    w->Xb = cv.take<__nv_bfloat16>((size_t)npad * dpad);
+    w->Eb = cv.take<__nv_bfloat16>((size_t)cpad * dpad);
+    w->enrm = cv.take<float>(cpad);
+    w->arg = cv.take<int32_t>(n);
+    w->err = cv.take<int32_t>(1);
+    return cv.used;
+}
+
+}  // namespace apgb
+
+APGB_API size_t lap_assign_workspace_size(int64_t n, int64_t d, int64_t c) {
+    if (n < 1 || d < 1 || c < 1 || c > n || n > INT_MAX / 2 || d > 65536) return 0;
+    AssignWs w;
+    return carve_assign(nullptr, n, d, c, &w);
+}
+
+APGB_API int32_t lap_assign(const float* X, int64_t n, int64_t d, int64_t ldx, const int32_t* centres,
+                            int64_t c, int32_t* idx, float* best, void* ws, size_t ws_bytes,
+                            void* stream) {
+    if (!X || !centres || !idx || ldx < d || !lap_assign_workspace_size(n, d, c))
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    AssignWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_assign(nullptr, n, d, c, &w)));
+    carve_assign(ws, n, d, c, &w);
+    const int di = (int)d, dpad = (di + 63) / 64 * 64;
+    const int64_t npad = (n + 127) / 128 * 128, cpad = (c + 255) / 256 * 256;
+    AP_TRY(column_means(X, n, di, ldx, w.part, w.mean, s));
+    centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, nullptr, n, npad, dpad, w.mean, w.Xb, nullptr);
+    centre_bf16_kernel<<<(int)std::min<int64_t>((cpad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, centres, c, cpad, dpad, w.mean, w.Eb, w.enrm);
+    AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+    note_launches(2);
+    AP_TRY(last_error());
+    AP_TRY(tc_assign_argmax(w.Xb, (int)n, w.Eb, (int)c, w.enrm, dpad, w.arg, best, w.err, s));
+    const int lgrid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    labels_kernel<<<lgrid, 256, 0, s>>>(w.arg, n, centres, idx);
+    exemplars_keep_self_kernel<<<(int)((c + 255) / 256), 256, 0, s>>>(centres, (int)c, idx);
+    note_launches(2);
+    AP_TRY(last_error());
+    int32_t err = 0;
+    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    return err ? AP_ERR_TIMEOUT : AP_OK;
+}
+
 // ---- Algorithm 3, Steps 1-4 --------------------------------------------------------------
 namespace apgb {
 
@@ -589,6 +790,12 @@ struct LapFullWs {
     void* sub;
     size_t sub_bytes;
     int64_t emax;
+    // Step 4's refinement
+    int32_t *j2, *cls, *nosecond, *cand, *blocked, *counts, *medoid;
+    float *s1, *s2;
+    double *dist, *mu;
+    unsigned long long *delta, *sums, *mind;
+    unsigned* absmax;
 };
 
 static size_t carve_lap_full(void* ws, int64_t n, int64_t d, int64_t L, int64_t m0,
@@ -625,6 +832,21 @@ static size_t carve_lap_full(void* ws, int64_t n, int64_t d, int64_t L, int64_t 
     w->sub = c.take<char>(sub);
     w->sub_bytes = sub;
     w->emax = emax;
+    w->j2 = c.take<int32_t>(n);
+    w->cls = c.take<int32_t>(n);
+    w->s1 = c.take<float>(n);
+    w->s2 = c.take<float>(n);
+    w->dist = c.take<double>(n);
+    w->nosecond = c.take<int32_t>(emax);
+    w->cand = c.take<int32_t>(emax);
+    w->blocked = c.take<int32_t>(emax);
+    w->counts = c.take<int32_t>(emax);
+    w->medoid = c.take<int32_t>(emax);
+    w->delta = c.take<unsigned long long>(emax);
+    w->mind = c.take<unsigned long long>(emax);
+    w->sums = c.take<unsigned long long>((size_t)emax * d);
+    w->mu = c.take<double>((size_t)emax * d);
+    w->absmax = c.take<unsigned>(1);
     return (lap_bytes && sub) ? c.used : 0;
 }
 
@@ -650,6 +872,116 @@ static int32_t landmark_ap(const LapWs& w, int64_t L, int64_t d, int32_t precisi
 
 }  // namespace apgb
 
+namespace apgb {
+
+// The buffers of Step 4's refinement (device; n points, emax centres at most).
+struct RefineView {
+    const __nv_bfloat16* Xb;    // the points' bf16 centred features [npad x dpad]
+    const float* mean;          // the mean they were centred on
+    int32_t* E;                 // the centre list
+    __nv_bfloat16* Eb;
+    float* enrm;
+    int32_t *j1, *j2, *cls, *nosecond, *cand, *blocked, *counts, *medoid;
+    float *s1, *s2;
+    double *dist, *mu;
+    unsigned long long *delta, *sums, *mind;
+    unsigned* absmax;
+    int32_t* err;
+};
+
+struct RefineStats {
+    int32_t rounds = 0, removed = 0, moved = 0;
+};
+
+// Step 4's refinement (Algorithm 3): rounds of a local search on net
+// similarity over the centres E (v.E, *nE entries, ascending; *hE its host
+// copy).  A round: nearest and second-nearest centre of every point
+// (tensor-core GEMM, top-2 epilogue); the cost of dropping each centre
+// (what its class loses moving to second choices); dropping the
+// candidates (cost below -p) that no cheaper conflicting candidate blocks;
+// every class's centre moved to the member nearest the class mean.  Stops
+// after a round that changes nothing, or after `rounds` rounds.
+static int32_t refine_centres(const float* X, int64_t n, int di, int64_t ldx, int dpad, float p, int rounds,
+                              const RefineView& w, int64_t* nE, std::vector<int32_t>* hE,
+                              RefineStats* st, cudaStream_t s) {
+    // fixed-point scale of the class sums: |sum| <= n max|x| must stay below 2^62
+    AP_CUDA_TRY(cudaMemsetAsync(w.absmax, 0, sizeof(unsigned), s));
+    absmax_kernel<<<(int)std::min<int64_t>((n * di + 255) / 256, 4096), 256, 0, s>>>(X, n, di, ldx, w.absmax);
+    note_launches(1);
+    AP_TRY(last_error());
+    unsigned abits = 0;
+    AP_CUDA_TRY(cudaMemcpyAsync(&abits, w.absmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    float amax;
+    std::memcpy(&amax, &abits, sizeof(float));
+    if (!std::isfinite(amax)) return AP_ERR_INVALID_ARG;
+    int sc = 32;
+    while (sc > 0 && std::ldexp((double)amax * (double)n + 1.0, sc) > 4.0e18) --sc;
+    const double scale = std::ldexp(1.0, sc);
+    const int grid_n = grid_for(n);
+    const int grid_w = (int)std::min<int64_t>((n + 7) / 8, 65535);
+    for (int r = 0; r < rounds; ++r) {
+        const int c = (int)*nE;
+        const int64_t epad = ((int64_t)c + 255) / 256 * 256;
+        centre_bf16_kernel<<<(int)std::min<int64_t>((epad + 7) / 8, 65535), 256, 0, s>>>(
+            X, ldx, di, w.E, c, epad, dpad, w.mean, w.Eb, w.enrm);
+        AP_CUDA_TRY(cudaMemsetAsync(w.nosecond, 0, sizeof(int32_t) * c, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.blocked, 0, sizeof(int32_t) * c, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * c, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.delta, 0, sizeof(unsigned long long) * c, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.mind, 0xFF, sizeof(unsigned long long) * c, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.medoid, 0x7F, sizeof(int32_t) * c, s));
+        AP_CUDA_TRY(cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * c * di, s));
+        note_launches(1);
+        AP_TRY(last_error());
+        AP_TRY(tc_assign_top2(w.Xb, (int)n, w.Eb, c, w.enrm, dpad, w.j1, w.s1, w.j2, w.s2,
+                              w.err, s));
+        refine_costs_kernel<<<grid_n, 256, 0, s>>>(n, w.j1, w.s1, w.j2, w.s2, w.delta, w.nosecond);
+        refine_candidates_kernel<<<(c + 255) / 256, 256, 0, s>>>(c, w.delta, w.nosecond,
+                                                                 -(double)p * kDeltaUnit, w.cand);
+        refine_block_kernel<<<grid_n, 256, 0, s>>>(n, w.j1, w.j2, w.cand, w.delta, w.blocked);
+        refine_classes_kernel<<<grid_n, 256, 0, s>>>(n, w.j1, w.j2, w.cand, w.blocked, w.cls, w.counts);
+        class_sum_kernel<<<grid_w, 256, 0, s>>>(X, ldx, di, n, w.cls, scale, w.sums);
+        class_mean_kernel<<<(int)std::min<int64_t>(((int64_t)c * di + 255) / 256, 4096), 256, 0, s>>>(
+            c, di, w.sums, w.counts, 1.0 / scale, w.mu);
+        class_dist_kernel<<<grid_w, 256, 0, s>>>(X, ldx, di, n, w.cls, w.mu, w.dist, w.mind);
+        class_argmin_kernel<<<grid_n, 256, 0, s>>>(n, w.cls, w.dist, w.mind, w.medoid);
+        note_launches(8);
+        AP_TRY(last_error());
+        std::vector<int32_t> cand(c), blocked(c), counts(c), medoid(c);
+        AP_CUDA_TRY(cudaMemcpyAsync(cand.data(), w.cand, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaMemcpyAsync(blocked.data(), w.blocked, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaMemcpyAsync(counts.data(), w.counts, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaMemcpyAsync(medoid.data(), w.medoid, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
+        int32_t err = 0;
+        AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (err) return AP_ERR_TIMEOUT;
+        std::vector<int32_t> next;
+        next.reserve(c);
+        int removed = 0, moved = 0;
+        for (int j = 0; j < c; ++j) {
+            if ((cand[j] && !blocked[j]) || counts[j] == 0) {      // dropped (or left empty)
+                ++removed;
+                continue;
+            }
+            moved += medoid[j] != (*hE)[j];
+            next.push_back(medoid[j]);
+        }
+        st->rounds = r + 1;
+        st->removed += removed;
+        st->moved += moved;
+        if (removed == 0 && moved == 0) break;
+        std::sort(next.begin(), next.end());
+        *hE = next;
+        *nE = (int64_t)next.size();
+        AP_CUDA_TRY(cudaMemcpyAsync(w.E, hE->data(), sizeof(int32_t) * next.size(), cudaMemcpyHostToDevice, s));
+    }
+    return AP_OK;
+}
+
+}  // namespace apgb
+
 APGB_API size_t lap_run_full_workspace_size(int64_t n, int64_t d, int64_t n_landmarks, int64_t m0,
                                             int32_t max_levels) {
     if (n < 2 || d < 1 || n_landmarks < 2 || n_landmarks > n || m0 < 2 || m0 > n ||
@@ -661,12 +993,13 @@ APGB_API size_t lap_run_full_workspace_size(int64_t n, int64_t d, int64_t n_land
 
 APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t L,
                               int64_t m0, uint64_t seed, int32_t precision, const ap_params* params,
-                              int32_t max_levels, int32_t* idx, int32_t* level_of,
+                              int32_t max_levels, int32_t refine_rounds, int32_t* idx, int32_t* level_of,
                               lap_full_result* out, void* ws, size_t ws_bytes, void* stream) {
     if (!X || !idx || !out || !params || ldx < d ||
         !lap_run_full_workspace_size(n, d, L, m0, max_levels))
         return AP_ERR_INVALID_ARG;
     if (precision != AP_PREC_FP32 && precision != AP_PREC_BF16) return AP_ERR_INVALID_ARG;
+    if (refine_rounds < 0) return AP_ERR_INVALID_ARG;
     AP_TRY(require_sm103());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     LapFullWs w;
@@ -725,7 +1058,7 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
                 set_level_kernel<<<grid_for(nl), 256, 0, s>>>(ids, nl, level, level_of);
                 note_launches(1);
             }
-            if (nE + added > w.emax) return AP_ERR_TOO_LARGE;
+            if (nE + added > w.emax) return AP_ERR_CAPACITY;
             nE += added;
             out->exemplars_at[level] = added;
             break;
@@ -775,7 +1108,7 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
         flag_rows_kernel<<<grid_for(Ll), 256, 0, s>>>(w.lap.lm, Ll, w.is_lm);
         gate_kernel<<<grid_for(nl), 256, 0, s>>>(nl, w.lap.arg, w.best, w.xnrm, w.maxd, w.is_lm, ids,
                                                  level, w.un, level_of);
-        if (nE + c > w.emax) return AP_ERR_TOO_LARGE;
+        if (nE + c > w.emax) return AP_ERR_CAPACITY;
         map_ids_kernel<<<grid_for(c), 256, 0, s>>>(w.lap.epts, c, ids, w.E + nE, level, level_of);
         nE += c;
         out->exemplars_at[level] = c;
@@ -807,12 +1140,24 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
     std::sort(hE.begin(), hE.end());
     AP_CUDA_TRY(cudaMemcpyAsync(w.E, hE.data(), sizeof(int32_t) * nE, cudaMemcpyHostToDevice, s));
     AP_TRY(column_means(X, n, di, ldx, w.lap.part, w.lap.mean, s));
-    const int64_t npad = (n + 127) / 128 * 128, epad = (nE + 255) / 256 * 256;
+    const int64_t npad = (n + 127) / 128 * 128;
     centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
         X, ldx, di, nullptr, n, npad, dpad, w.lap.mean, w.lap.Xb, nullptr);
+    note_launches(1);
+    if (refine_rounds > 0) {
+        RefineView v{w.lap.Xb, w.lap.mean, w.E, w.Eb, w.enrm, w.lap.arg, w.j2, w.cls, w.nosecond, w.cand,
+                     w.blocked, w.counts, w.medoid, w.s1, w.s2, w.dist, w.mu, w.delta, w.sums, w.mind,
+                     w.absmax, w.lap.err};
+        RefineStats rs;
+        AP_TRY(refine_centres(X, n, di, ldx, dpad, p, refine_rounds, v, &nE, &hE, &rs, s));
+        out->refine_rounds = rs.rounds;
+        out->refine_removed = rs.removed;
+        out->refine_moved = rs.moved;
+    }
+    const int64_t epad = (nE + 255) / 256 * 256;
     centre_bf16_kernel<<<(int)std::min<int64_t>((epad + 7) / 8, 65535), 256, 0, s>>>(
         X, ldx, di, w.E, nE, epad, dpad, w.lap.mean, w.Eb, w.enrm);
-    note_launches(2);
+    note_launches(1);
     AP_TRY(last_error());
     AP_TRY(tc_assign_argmax(w.lap.Xb, (int)n, w.Eb, (int)nE, w.enrm, dpad, w.lap.arg, nullptr,
                             w.lap.err, s));
@@ -835,6 +1180,121 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
     out->n_exemplars = (int32_t)nE;
     out->dpsim = dps;
     out->expref = (double)p * (double)nE;
+    out->netsim = out->dpsim + out->expref;
+    return AP_OK;
+}
+
+// ---- Algorithm 3 Step 4 alone: refinement of a given centre set ----------------------------
+namespace apgb {
+
+struct RefineWs {
+    double* part;
+    float* mean;
+    __nv_bfloat16 *Xb, *Eb;
+    float* enrm;
+    int32_t *E, *j1, *j2, *cls, *nosecond, *cand, *blocked, *counts, *medoid;
+    float *s1, *s2;
+    double *dist, *mu, *dp, *tot;
+    unsigned long long *delta, *sums, *mind;
+    unsigned* absmax;
+    int32_t* err;
+};
+
+static size_t carve_refine(void* ws, int64_t n, int64_t d, int64_t c, RefineWs* w) {
+    const int dpad = (int)((d + 63) / 64 * 64);
+    const int64_t npad = (n + 127) / 128 * 128, cpad = (c + 255) / 256 * 256;
+    Carver cv(ws);
+    w->part = cv.take<double>(column_mean_part_doubles(n, (int)d));
+    w->mean = cv.take<float>(d);
+    w->Xb = cv.take<__nv_bfloat16>((size_t)npad * dpad);
+    w->Eb = cv.take<__nv_bfloat16>((size_t)cpad * dpad);
+    w->enrm = cv.take<float>(cpad);
+    w->E = cv.take<int32_t>(c);
+    for (int32_t** q : {&w->j1, &w->j2, &w->cls}) *q = cv.take<int32_t>(n);
+    for (int32_t** q : {&w->nosecond, &w->cand, &w->blocked, &w->counts, &w->medoid}) *q = cv.take<int32_t>(c);
+    w->s1 = cv.take<float>(n);
+    w->s2 = cv.take<float>(n);
+    w->dist = cv.take<double>(n);
+    w->dp = cv.take<double>(n);
+    w->tot = cv.take<double>(1);
+    w->mu = cv.take<double>((size_t)c * d);
+    w->delta = cv.take<unsigned long long>(c);
+    w->mind = cv.take<unsigned long long>(c);
+    w->sums = cv.take<unsigned long long>((size_t)c * d);
+    w->absmax = cv.take<unsigned>(1);
+    w->err = cv.take<int32_t>(1);
+    return cv.used;
+}
+
+}  // namespace apgb
+
+APGB_API size_t lap_refine_workspace_size(int64_t n, int64_t d, int64_t c) {
+    if (n < 1 || d < 1 || c < 1 || c > n || n > INT_MAX / 2 || d > 65536) return 0;
+    RefineWs w;
+    return carve_refine(nullptr, n, d, c, &w);
+}
+
+APGB_API int32_t lap_refine(const float* X, int64_t n, int64_t d, int64_t ldx, const int32_t* centres,
+                            int64_t c, float pref, int32_t rounds, int32_t* centres_out, int32_t* idx,
+                            lap_refine_result* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!X || !centres || !centres_out || !idx || !out || ldx < d || rounds < 0 || !std::isfinite(pref) ||
+        !lap_refine_workspace_size(n, d, c))
+        return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RefineWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_refine(nullptr, n, d, c, &w)));
+    carve_refine(ws, n, d, c, &w);
+    const int di = (int)d, dpad = (di + 63) / 64 * 64;
+    // the centre list, ascending and distinct
+    std::vector<int32_t> hE(c);
+    AP_CUDA_TRY(cudaMemcpyAsync(hE.data(), centres, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    std::sort(hE.begin(), hE.end());
+    for (int64_t j = 0; j < c; ++j)
+        if (hE[j] < 0 || hE[j] >= n || (j > 0 && hE[j] == hE[j - 1])) return AP_ERR_INVALID_ARG;
+    AP_CUDA_TRY(cudaMemcpyAsync(w.E, hE.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
+    AP_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+    AP_TRY(column_means(X, n, di, ldx, w.part, w.mean, s));
+    const int64_t npad = (n + 127) / 128 * 128;
+    centre_bf16_kernel<<<(int)std::min<int64_t>((npad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, nullptr, n, npad, dpad, w.mean, w.Xb, nullptr);
+    note_launches(1);
+    AP_TRY(last_error());
+    int64_t nE = c;
+    RefineStats rs;
+    if (rounds > 0) {
+        RefineView v{w.Xb, w.mean, w.E, w.Eb, w.enrm, w.j1, w.j2, w.cls, w.nosecond, w.cand, w.blocked,
+                     w.counts, w.medoid, w.s1, w.s2, w.dist, w.mu, w.delta, w.sums, w.mind, w.absmax, w.err};
+        AP_TRY(refine_centres(X, n, di, ldx, dpad, pref, rounds, v, &nE, &hE, &rs, s));
+    }
+    // every point to its nearest centre of the final set; centres keep themselves
+    const int64_t epad = (nE + 255) / 256 * 256;
+    centre_bf16_kernel<<<(int)std::min<int64_t>((epad + 7) / 8, 65535), 256, 0, s>>>(
+        X, ldx, di, w.E, nE, epad, dpad, w.mean, w.Eb, w.enrm);
+    note_launches(1);
+    AP_TRY(last_error());
+    AP_TRY(tc_assign_argmax(w.Xb, (int)n, w.Eb, (int)nE, w.enrm, dpad, w.j1, nullptr, w.err, s));
+    labels_kernel<<<grid_for(n), 256, 0, s>>>(w.j1, n, w.E, idx);
+    exemplars_keep_self_kernel<<<(int)((nE + 255) / 256), 256, 0, s>>>(w.E, (int)nE, idx);
+    lap_dpsim_kernel<<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, s>>>(X, ldx, di, n, idx, w.dp);
+    sum_f64_kernel<<<1, 1024, 0, s>>>(w.dp, n, w.tot);
+    AP_CUDA_TRY(cudaMemcpyAsync(centres_out, w.E, sizeof(int32_t) * nE, cudaMemcpyDeviceToDevice, s));
+    note_launches(4);
+    AP_TRY(last_error());
+    double dps = 0.0;
+    int32_t err = 0;
+    AP_CUDA_TRY(cudaMemcpyAsync(&dps, w.tot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(&err, w.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return AP_ERR_TIMEOUT;
+    *out = lap_refine_result{};
+    out->rounds = rs.rounds;
+    out->removed = rs.removed;
+    out->moved = rs.moved;
+    out->n_exemplars = (int32_t)nE;
+    out->dpsim = dps;
+    out->expref = (double)pref * (double)nE;
     out->netsim = out->dpsim + out->expref;
     return AP_OK;
 }

@@ -87,6 +87,7 @@ APGB_API const char* ap_status_string(int32_t s) {
         case AP_ERR_NONFINITE: return "non-finite similarity";
         case AP_ERR_UNSUPPORTED: return "unsupported device or configuration";
         case AP_ERR_TOO_LARGE: return "problem larger than the built-in scratch of a no-allocation entry";
+        case AP_ERR_CAPACITY: return "a result outgrew the capacity its workspace was sized for";
         default: return "unknown status";
     }
 }

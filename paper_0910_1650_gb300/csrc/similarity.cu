@@ -29,6 +29,11 @@ namespace apgb {
 
 int32_t tc_similarity_bf16(const __nv_bfloat16* Xb, const float* nrm, int n, int dpad,
                            float* S, int64_t lds, int32_t* err, cudaStream_t s);
+size_t tc_grouped_table_bytes(const int64_t* n, int32_t count);
+int32_t tc_similarity_bf16_grouped(const __nv_bfloat16* Xb, const float* nrm, int64_t rows, int dpad,
+                                   const int64_t* n, const int64_t* roff, float* const* S,
+                                   const int64_t* lds, int32_t count, void* tables, int32_t* err,
+                                   cudaStream_t s);
 size_t tc_similarity_pad_rows();
 
 // ---- 1. column means -----------------------------------------------------------
@@ -509,6 +514,7 @@ struct SimProblem {
     SelectState* sel;
     unsigned long long* hist;
     float* pref;
+    int64_t roff;           // first row of the problem in the centred-feature arena
 };
 
 // The problem whose blocks (first block b0(P[b])) include block `blk`.
@@ -704,14 +710,23 @@ static int32_t sim_streams(std::array<cudaStream_t, kSimStreams>* out) {
 // pointers and block counts (problem fields filled by the caller).
 static size_t carve_batched(void* ws, const int64_t* n, int32_t count, int64_t d, int32_t precision,
                             SimProblem** table, std::vector<SimProblem>* host, int32_t** err,
-                            float** prefs) {
+                            float** prefs, void** tables) {
     Carver c(ws);
     SimProblem* t = c.take<SimProblem>((size_t)count);
     int32_t* e = c.take<int32_t>((size_t)count);
     float* pv = c.take<float>((size_t)count);
     const int dpad = pad_dim((int)d);
     const size_t esz = precision == AP_PREC_FP32 ? sizeof(float) : sizeof(__nv_bfloat16);
+    // every problem's centred rows (and norms) in one arena, problem b from row
+    // roff_b (a multiple of the tensor-core tile), so that one grouped launch
+    // covers the whole batch
+    int64_t rows = 0;
+    for (int32_t b = 0; b < count; ++b) rows += pad_rows((int)n[b]);
+    unsigned char* xc_arena = c.take<unsigned char>((size_t)rows * dpad * esz);
+    float* nrm_arena = c.take<float>((size_t)rows);
+    void* tab = c.take<unsigned char>(tc_grouped_table_bytes(n, count));
     int part_b0 = 0, centre_b0 = 0, hist_b0 = 0;
+    int64_t roff = 0;
     for (int32_t b = 0; b < count; ++b) {
         SimProblem q{};
         q.n = (int)n[b];
@@ -728,8 +743,10 @@ static size_t carve_batched(void* ws, const int64_t* n, int32_t count, int64_t d
         hist_b0 += q.hist_nb;
         q.part = c.take<double>((size_t)q.nb * d);
         q.mean = c.take<float>((size_t)d);
-        q.xc = c.take<unsigned char>((size_t)q.npad * dpad * esz);
-        q.nrm = c.take<float>((size_t)q.npad);
+        q.roff = roff;
+        q.xc = xc_arena ? xc_arena + (size_t)roff * dpad * esz : nullptr;
+        q.nrm = nrm_arena ? nrm_arena + roff : nullptr;
+        roff += q.npad;
         q.sel = c.take<SelectState>(1);
         q.hist = c.take<unsigned long long>(4096);
         q.pref = pv ? pv + b : nullptr;
@@ -738,6 +755,7 @@ static size_t carve_batched(void* ws, const int64_t* n, int32_t count, int64_t d
     if (table) *table = t;
     if (err) *err = e;
     if (prefs) *prefs = pv;
+    if (tables) *tables = tab;
     return c.used;
 }
 
@@ -756,7 +774,8 @@ static bool batched_args_ok(const int64_t* n, int32_t count, int64_t d) {
 APGB_API size_t ap_similarity_batched_workspace_size(const int64_t* n, int32_t count, int64_t d) {
     if (!batched_args_ok(n, count, d)) return 0;
     // the bf16 centred copy is the smaller; size for float32 so one query serves both
-    return carve_batched(nullptr, n, count, d, AP_PREC_FP32, nullptr, nullptr, nullptr, nullptr);
+    return carve_batched(nullptr, n, count, d, AP_PREC_FP32, nullptr, nullptr, nullptr, nullptr,
+                         nullptr);
 }
 
 APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, const int64_t* n,
@@ -778,13 +797,12 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
     AP_TRY(require_sm103());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AP_TRY(check_ws(ws, ws_bytes, ap_similarity_batched_workspace_size(n, count, d)));
-    std::array<cudaStream_t, kSimStreams> ss;
-    AP_TRY(sim_streams(&ss));
     std::vector<SimProblem> host(count);
     SimProblem* table = nullptr;
     int32_t* err = nullptr;
     float* prefs = nullptr;
-    carve_batched(ws, n, count, d, precision, &table, &host, &err, &prefs);
+    void* tables = nullptr;
+    carve_batched(ws, n, count, d, precision, &table, &host, &err, &prefs, &tables);
     int part_blocks = 0, centre_blocks = 0, hist_blocks = 0;
     for (int32_t b = 0; b < count; ++b) {
         host[b].X = X + xoff[b];
@@ -812,28 +830,43 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
     }
     note_launches(3);
     AP_TRY(last_error());
-    // 3. the Gram products, forked over the library's streams
-    cudaEvent_t fork, join[kSimStreams];
-    AP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    for (auto& e : join) AP_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    struct Guard {
-        cudaEvent_t f;
-        cudaEvent_t* j;
-        ~Guard() {
-            cudaEventDestroy(f);
-            for (int k = 0; k < kSimStreams; ++k) cudaEventDestroy(j[k]);
+    // 3. the Gram products: bf16 as one persistent tensor-core launch over the
+    //    tiles of every problem; float32 forked over the library's streams
+    if (bf16) {
+        std::vector<int64_t> roffs(count), nn(count), ld(count);
+        std::vector<float*> Sp(count);
+        int64_t rows = 0;
+        for (int32_t b = 0; b < count; ++b) {
+            roffs[b] = host[b].roff;
+            nn[b] = host[b].n;
+            ld[b] = host[b].lds;
+            Sp[b] = host[b].S;
+            rows = host[b].roff + host[b].npad;
         }
-    } guard{fork, join};
-    AP_CUDA_TRY(cudaEventRecord(fork, s));
-    for (int k = 0; k < kSimStreams; ++k) AP_CUDA_TRY(cudaStreamWaitEvent(ss[k], fork, 0));
-    int32_t st = AP_OK;
-    for (int32_t b = 0; b < count && st == AP_OK; ++b) {
-        const SimProblem& q = host[b];
-        cudaStream_t sk = ss[b % kSimStreams];
-        if (bf16) {
-            st = tc_similarity_bf16(static_cast<const __nv_bfloat16*>(q.xc), q.nrm, q.n, dpad, q.S, q.lds,
-                                    err + b, sk);
-        } else {
+        if (!vec) return AP_ERR_INVALID_ARG;         // TMA stores need aligned rows
+        AP_TRY(tc_similarity_bf16_grouped(static_cast<const __nv_bfloat16*>(host[0].xc), host[0].nrm, rows,
+                                          dpad, nn.data(), roffs.data(), Sp.data(), ld.data(), count,
+                                          tables, err, s));
+    } else {
+        std::array<cudaStream_t, kSimStreams> ss;
+        AP_TRY(sim_streams(&ss));
+        cudaEvent_t fork, join[kSimStreams];
+        AP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (auto& e : join) AP_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        struct Guard {
+            cudaEvent_t f;
+            cudaEvent_t* j;
+            ~Guard() {
+                cudaEventDestroy(f);
+                for (int k = 0; k < kSimStreams; ++k) cudaEventDestroy(j[k]);
+            }
+        } guard{fork, join};
+        AP_CUDA_TRY(cudaEventRecord(fork, s));
+        for (int k = 0; k < kSimStreams; ++k) AP_CUDA_TRY(cudaStreamWaitEvent(ss[k], fork, 0));
+        int32_t st = AP_OK;
+        for (int32_t b = 0; b < count && st == AP_OK; ++b) {
+            const SimProblem& q = host[b];
+            cudaStream_t sk = ss[b % kSimStreams];
             dim3 grid((q.n + GT - 1) / GT, (q.n + GT - 1) / GT);
             const int vec_ok = aligned16(q.S) && (q.lds & 3) == 0;
             sim_gemm_fp32_kernel<<<grid, 256, 0, sk>>>(static_cast<const float*>(q.xc), q.n, dpad, q.nrm,
@@ -841,13 +874,13 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
             note_launches(1);
             st = last_error();
         }
+        // join: the caller's stream continues after every worker (also on error)
+        for (int k = 0; k < kSimStreams; ++k) {
+            AP_CUDA_TRY(cudaEventRecord(join[k], ss[k]));
+            AP_CUDA_TRY(cudaStreamWaitEvent(s, join[k], 0));
+        }
+        AP_TRY(st);
     }
-    // join: the caller's stream continues after every worker (also on error)
-    for (int k = 0; k < kSimStreams; ++k) {
-        AP_CUDA_TRY(cudaEventRecord(join[k], ss[k]));
-        AP_CUDA_TRY(cudaStreamWaitEvent(s, join[k], 0));
-    }
-    AP_TRY(st);
     // 4-5. the preferences and the diagonals
     const int dgy = (int)std::min<int64_t>((nmax + 255) / 256, 65535);
     if (pref_mode == AP_PREF_MEDIAN) {

@@ -42,7 +42,13 @@ def test_score_landmarks_exact():
     assert np.array_equal(lm.cpu().numpy().astype(np.int64), np.sort(order[:L]))
 
 
-def _check_assignment(X, E_pts, labels):
+def _check_assignment(X, E_pts, labels, best=None):
+    """Labels against the oracle's distances of the bf16-rounded centred
+    points: exact wherever the best distance beats the runner-up by more
+    than the float32 accumulation bound, within that bound elsewhere.
+    Returns (share of the non-centre points with a clear decision, share of
+    their labels that differ from the float64 nearest centre of the unrounded
+    points)."""
     Xt = oap.round_bf16(oap.centred(X)).astype(np.float64)
     Et = Xt[E_pts]
     D = -oap.similarity(Xt, Et)
@@ -54,13 +60,70 @@ def _check_assignment(X, E_pts, labels):
     is_ex = np.zeros(X.shape[0], dtype=bool)
     is_ex[E_pts] = True
     got = np.array([pos[int(c)] for c in labels])
-    best = D.min(axis=1)
-    assert (D[np.arange(len(got)), got] <= best + tol).all()
-    srt = np.sort(D, axis=1)
-    clear = (srt[:, 1] - srt[:, 0] > 2 * tol) & ~is_ex
+    best_d = D.min(axis=1)
+    assert (D[np.arange(len(got)), got] <= best_d + tol).all()
+    if D.shape[1] > 1:
+        srt = np.sort(D, axis=1)
+        clear = (srt[:, 1] - srt[:, 0] > 2 * tol) & ~is_ex
+    else:
+        clear = ~is_ex
     assert np.array_equal(got[clear], D.argmin(axis=1)[clear])
     assert (labels[E_pts] == E_pts).all()
-    return clear.mean()
+    if best is not None:
+        # the reported score is 2 x.e - |e|^2 of the chosen centre
+        ref = nx - best_d
+        assert np.all(np.abs(best - ref) <= tol + 1e-6 * np.abs(ref))
+    # the paper's distance: plain float64 squared distance of the unrounded points
+    D64 = -oap.similarity(X.astype(np.float64), X[E_pts].astype(np.float64))
+    near64 = D64.argmin(axis=1)
+    differ = (near64 != got) & ~is_ex
+    nonex = max(1, (~is_ex).sum())
+    return clear.sum() / nonex, differ.sum() / nonex
+
+
+@pytest.mark.parametrize("c_case,n,c,seed", [("mix128", 8000, 700, 1), ("mix128", 3001, 257, 2),
+                                           ("mix128", 513, 256, 3), ("mix128", 1000, 1, 4),
+                                           ("subspace100", 5000, 600, 5)])
+def test_lap_assign_full_shape(c_case, n, c, seed):
+    """The assignment GEMM's arg-max mode through its own entry (Algorithm 3
+    Step 2) at the shapes of the 1e6-point workload: d = 128 (two K blocks)
+    or d = 100 (zero-padded K), up to three 256-column tiles of centres
+    merged by the running arg-max, and dozens of 128-row blocks."""
+    if c_case == "mix128":
+        X, _ = synth.workload(3, scale=n / 1_000_000)
+    else:
+        X, _ = synth.workload(2, scale=n / 60000)
+    X = np.ascontiguousarray(X[:n])
+    g = np.random.default_rng(seed)
+    E = g.choice(n, c, replace=False).astype(np.int64)        # list order = tie order
+    idx, best = capi.lap_assign(torch.from_numpy(X).cuda(), torch.from_numpy(E), best=True)
+    labels = idx.cpu().numpy().astype(np.int64)
+    assert set(np.unique(labels).tolist()) <= set(E.tolist())
+    frac_clear, frac_fp64 = _check_assignment(X, E, labels, best.cpu().numpy().astype(np.float64))
+    print(f"\nlap_assign n={n} c={c} d={X.shape[1]}: clear {frac_clear:.4f}, "
+          f"differ from float64 unrounded {frac_fp64:.2e}")
+    # random centres put several centres in one cluster: near ties (within
+    # rounding) are common, and every clear decision is still checked exactly
+    assert frac_clear > 0.8
+    assert frac_fp64 <= 0.02
+
+
+def test_lap_run_full_shape_assignment():
+    """lap_run (Steps 1-2) on 20000 points of the 1e6-point 128-D workload
+    generator with 3000 uniform landmarks: several hundred exemplars (three or
+    more 256-column tiles), 157 row blocks.  The landmark problem runs on the
+    GPU; Step 2's labels are checked against the oracle's nearest exemplar."""
+    X, _ = synth.workload(3, scale=0.02)
+    idx, lm, res = capi.lap_run(torch.from_numpy(X).cuda(), 3000, "uniform", seed=5,
+                                damping=0.9, max_iter=1000, conv_iter=15)
+    labels = idx.cpu().numpy().astype(np.int64)
+    E = np.unique(labels)
+    assert E.size == res["n_exemplars"] >= 600
+    frac_clear, frac_fp64 = _check_assignment(X, E, labels)
+    print(f"\nlap_run n=20000 d=128 exemplars={E.size}: clear {frac_clear:.4f}, "
+          f"differ from float64 unrounded {frac_fp64:.2e}")
+    assert frac_clear > 0.99
+    assert frac_fp64 <= 0.001
 
 
 def test_lap_matches_oracle():
@@ -73,7 +136,7 @@ def test_lap_matches_oracle():
     labels = idx.cpu().numpy().astype(np.int64)
     E = np.unique(labels)
     assert np.array_equal(E, ref["E"]) and res["n_exemplars"] == E.size
-    frac_clear = _check_assignment(X, E, labels)
+    frac_clear, _ = _check_assignment(X, E, labels)
     assert frac_clear > 0.99
     # netsim of the GPU labelling, recomputed in float64 by the oracle
     S_all = None
@@ -169,3 +232,81 @@ def test_lap_full_recursion_and_invariants():
     assert np.all(idx[2990:] >= 2990)
     assert level_of.min() >= -1 and level_of.max() <= res["levels"]
     _check_assignment(X, E, idx)
+
+
+# ---- Algorithm 3 Step 4: the refinement ------------------------------------------------------
+
+def _integer_clusters(seed, k=20, per=30, d=16, spread=3):
+    """Integer points symmetric about the origin (k clusters mirrored): the
+    column mean is exactly zero and every coordinate, product and partial
+    sum is exact in bf16 / fp32, so the GPU's distances are the exact ones
+    and every decision (ties included) must be the oracle's."""
+    g = np.random.default_rng(seed)
+    C = g.integers(-60, 61, size=(k, d))
+    P = np.concatenate([c + g.integers(-spread, spread + 1, size=(per, d)) for c in C])
+    return np.vstack([P, -P]).astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", [3, 4, 6])
+def test_lap_refine_matches_oracle_exactly_on_integer_data(seed):
+    """The refinement against the oracle's, decision for decision: seeds whose
+    medoid choices are all clear (two members at the same distance from the
+    class mean in exact arithmetic may round apart differently under the two
+    summation orders; the precondition is asserted)."""
+    X = _integer_clusters(seed, spread=5)
+    n = X.shape[0]
+    g = np.random.default_rng(50 + seed)
+    E0 = g.choice(n, 90, replace=False)                      # about two centres per cluster
+    p = -300.5                                                # half-integer: no cost ties the threshold
+    E_ref, hist = olap.refine(X, E0, p, max_rounds=30)
+    assert min(h["medoid_gap"] for h in hist) > 1e-9          # every medoid choice is clear
+    E, idx, res = capi.lap_refine(torch.from_numpy(X).cuda(), torch.from_numpy(E0), p, rounds=30)
+    E = E.cpu().numpy().astype(np.int64)
+    assert np.array_equal(E, E_ref)
+    assert res["rounds"] == len(hist)
+    assert res["removed"] == sum(h["removed"] for h in hist)
+    assert res["moved"] == sum(h["moved"] for h in hist)
+    # final labels: nearest centre (exact distances, lowest index on ties); centres keep themselves
+    X64 = X.astype(np.float64)
+    D = ((X64[:, None, :] - X64[None, E_ref, :]) ** 2).sum(axis=2)
+    lab = E_ref[np.argmin(D, axis=1)]
+    lab[E_ref] = E_ref
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), lab)
+    dp = -D.min(axis=1)
+    dp[E_ref] = 0.0
+    assert res["netsim"] == pytest.approx(dp.sum() + p * E_ref.size, rel=1e-12)
+    assert res["netsim"] >= hist[0]["netsim"]
+
+
+def test_lap_refine_zero_rounds_is_the_assignment():
+    X, _ = synth.workload(3, scale=0.005)
+    E0 = np.random.default_rng(9).choice(X.shape[0], 300, replace=False)
+    Xd = torch.from_numpy(X).cuda()
+    E, idx, res = capi.lap_refine(Xd, torch.from_numpy(E0), -4000.0, rounds=0)
+    assert res["rounds"] == 0 and res["n_exemplars"] == 300
+    assert np.array_equal(E.cpu().numpy(), np.sort(E0))
+    idx2 = capi.lap_assign(Xd, torch.from_numpy(np.sort(E0)))
+    assert torch.equal(idx, idx2)
+
+
+def test_lap_full_refinement_raises_netsim_on_the_landmark_workload():
+    """Steps 1-4 on 30000 points of the 1e6-point generator: the gate leaves
+    the outskirts of every class to Step 3, whose exemplars duplicate
+    classes.  The refinement must not lower net similarity, must drop
+    exemplars, and its labels must be the nearest of the final exemplars."""
+    X, _ = synth.workload(3, scale=0.03)
+    Xd = torch.from_numpy(X).cuda()
+    kw = dict(seed=7, precision="bf16", damping=0.9, max_iter=1000, conv_iter=15)
+    idx0, _, r0 = capi.lap_run_full(Xd, 6000, 6000, refine_rounds=0, **kw)
+    idx1, _, r1 = capi.lap_run_full(Xd, 6000, 6000, refine_rounds=8, **kw)
+    print(f"\nlap_run_full 30000 points: exemplars {r0['n_exemplars']} -> {r1['n_exemplars']}, "
+          f"netsim {r0['netsim']:.6g} -> {r1['netsim']:.6g}, rounds {r1['refine_rounds']} "
+          f"removed {r1['refine_removed']} moved {r1['refine_moved']}")
+    assert r1["refine_rounds"] >= 1 and r1["refine_removed"] > 0
+    assert r1["n_exemplars"] < r0["n_exemplars"]
+    assert r1["netsim"] > r0["netsim"]
+    labels = idx1.cpu().numpy().astype(np.int64)
+    E = np.unique(labels)
+    assert E.size == r1["n_exemplars"]
+    frac_clear, _ = _check_assignment(X, E, labels)
+    assert frac_clear > 0.95

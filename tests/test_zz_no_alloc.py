@@ -28,6 +28,14 @@ def _case(X, iters, lam):
     return _square(S), _square(ref["R"]), _square(ref["A"])
 
 
+def _oracle_outputs(S, R, A):
+    """The oracle's outputs on the very float32 bits the GPU sees, with the
+    a+r decisions taken in float32 as the kernels take them."""
+    n = S.shape[0]
+    f = lambda t: t.cpu().numpy()[:, :n].astype(np.float64)
+    return oap.exemplars(f(S), f(R), f(A), dtype=np.float32)
+
+
 def test_noalloc_matches_workspace_entry_two_calls_in_a_row():
     X1, _ = synth.gaussian_mixture_2d()                 # n = 500
     X2, _ = synth.workload(1, scale=0.1)                # n = 2000, d = 64
@@ -49,6 +57,12 @@ def test_noalloc_matches_workspace_entry_two_calls_in_a_row():
         assert got["n_exemplars"] == ref["n_exemplars"] > 0
         for k in ("dpsim", "expref", "netsim"):
             assert abs(got[k] - ref[k]) <= 1e-12 * abs(ref[k])
+        # and what the oracle computes from the same messages
+        ora = _oracle_outputs(S, R, A)
+        assert np.array_equal(idx.cpu().numpy().astype(np.int64), ora["idx"])
+        assert got["n_exemplars"] == ora["E"].size
+        for k in ("dpsim", "expref", "netsim"):
+            assert abs(got[k] - ora[k]) <= 1e-9 * abs(ora[k])
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
