@@ -421,14 +421,16 @@ int32_t   lap_refine(const float* X, int64_t n, int64_t d, int64_t ldx, const in
  *   23    D(k) - max D(j) over the 16 neighbours j of features 0-15, where
  *         D = feature 20;
  *   24    the fraction of those neighbours with D(j) > D(k).
- * Network 25 -> 256 -> 256 -> 3 with ReLU; outputs (r_hat, a_hat, logit):
- * predicted converged r(k,k)/scale, a(k,k)/scale and exemplar log-odds.
+ * Network 25 -> 256 -> 256 -> 3 with ReLU; outputs (c_hat, a_hat, logit):
+ * the predicted converged column value min(0, r(k,k) + a(k,k))/scale (what
+ * the warm start writes into column k), a(k,k)/scale and the exemplar
+ * log-odds.
  * The input is first standardised, x -> (x - mu) * isd, with mu and isd
  * fixed (set by the caller from training features; their gradient is zero).
  * Parameters: one flat float32 vector of apl_param_count() entries (W1 256x25,
  * b1, W2 256x256, b2, W3 3x256, b3, mu 25, isd 25, row-major), plus a bf16
  * copy (same offsets) that the products use with fp32 accumulation.
- * Training loss (mean over rows): (r_hat - t_r)^2 + (a_hat - t_a)^2 +
+ * Training loss (mean over rows): (c_hat - t_c)^2 + (a_hat - t_a)^2 +
  * softplus(logit) - t_e * logit; Adam (0.9, 0.999, 1e-8, bias-corrected).
  * All device pointers are caller-owned; rows-sized scratch comes from `ws`
  * (apl_workspace_size(rows) bytes).  The calls below enqueue work only.
@@ -456,10 +458,32 @@ int32_t   apl_train_step(float* P, void* P16, float* M, float* V, int64_t step, 
                          void* ws, size_t ws_bytes, void* stream);
 /* R <- 0; A <- the column-constant availabilities of the predictions: at a
  * fixed point of Eq. 3-4, a(k,k) = colp(k) and a(i,k) = min(0, r(k,k) +
- * colp(k)) up to the i-th term, so A(i,k) = min(0, (r_hat_k + a_hat_k) *
- * scale) for i != k and A(k,k) = max(0, a_hat_k * scale). */
+ * colp(k)) up to the i-th term, so A(i,k) = min(0, c_hat_k * scale) for
+ * i != k and A(k,k) = max(0, a_hat_k * scale). */
 int32_t   apl_warm_start(const float* Y, int64_t n, float scale, float* R, float* A, int64_t ld,
                          void* stream);
+
+/* apl_warm_start_batched: features, forward pass and warm start of every
+ * problem of a batch in one call.  Problem b's S, R and A are n[b] x n[b]
+ * (row stride ld[b]) at element offset offsets[b] of the arenas S, R, A;
+ * scale: host float[count] (each problem's |preference|).  R <- 0 and A <-
+ * the column-constant availabilities of apl_warm_start, per problem.  Y:
+ * device float [sum n x 3] out (the predictions, problem after problem) or
+ * NULL.  ws: apl_warm_start_batched_workspace_size(n, count) bytes.
+ * Features are those of apl_features bit for bit; enqueues work only. */
+size_t    apl_warm_start_batched_workspace_size(const int64_t* n, int32_t count);
+int32_t   apl_warm_start_batched(const float* S, float* R, float* A, const int64_t* offsets,
+                                 const int64_t* n, const int64_t* ld, int32_t count,
+                                 const float* scale, const float* P, const void* P16, float* Y,
+                                 void* ws, size_t ws_bytes, void* stream);
+/* The network's input standardisation from training features F [rows x 25]:
+ * mu = column means, isd = 1 / max(population std, 1e-3), written into P's
+ * mu / isd slots (float64 sums in a fixed order).  Enqueues work only. */
+int32_t   apl_set_standardisation(float* P, const float* F, int64_t rows, void* stream);
+/* The judge (host only): use_warm[b] = 1 when |warm - cold| <= tol |cold|
+ * (both finite), else 0.  Returns the number of warm results kept. */
+int32_t   apl_judge(const double* cold_netsim, const double* warm_netsim, int32_t count,
+                    double tol, int32_t* use_warm);
 
 /* apl_ap_run: features -> network -> warm start -> Algorithm 1 -> outputs.
  * With judge != 0 it also runs Algorithm 1 from R = A = 0 (the method without

@@ -14,9 +14,10 @@ Per point k of a similarity matrix S with preference scale p > 0:
   (with fewer than 16 off-diagonal entries the last one is repeated, value
   and index);
   network: 25 -> 256 -> 256 -> 3, ReLU after the two hidden layers;
-  outputs: (r_hat, a_hat, logit): predicted converged r(k,k)/p, a(k,k)/p and
-  the log-odds that k is an exemplar;
-  loss (mean over rows): (r_hat - t_r)^2 + (a_hat - t_a)^2
+  outputs: (c_hat, a_hat, logit): the predicted converged column value
+  min(0, r(k,k) + a(k,k))/p (what the warm start writes into column k), the
+  predicted a(k,k)/p and the log-odds that k is an exemplar;
+  loss (mean over rows): (c_hat - t_c)^2 + (a_hat - t_a)^2
                          + softplus(logit) - t_e * logit   (binary cross-entropy);
   optimiser: Adam (Kingma & Ba 2015), beta1 0.9, beta2 0.999, eps 1e-8, with
   bias correction.
@@ -85,10 +86,12 @@ def row_features(S, scale):
 
 
 def targets(R, A, scale):
-    """(r(k,k)/p, a(k,k)/p, [k is an exemplar]) from converged messages."""
+    """(min(0, r(k,k) + a(k,k))/p, a(k,k)/p, [k is an exemplar]) from
+    converged messages."""
     n = R.shape[0]
     E = ap.exemplar_mask(R, A)
-    return np.stack([np.diag(R) / scale, np.diag(A) / scale, E.astype(np.float64)], axis=1)
+    c = np.minimum(0.0, np.diag(R) + np.diag(A))
+    return np.stack([c / scale, np.diag(A) / scale, E.astype(np.float64)], axis=1)
 
 
 def _w(Pd, bf16):
@@ -99,7 +102,7 @@ def _w(Pd, bf16):
 
 
 def forward(P, F, bf16=False):
-    """Returns (Y, cache).  Y: (rows, 3) = (r_hat, a_hat, logit)."""
+    """Returns (Y, cache).  Y: (rows, 3) = (c_hat, a_hat, logit)."""
     Pd = unpack(P)
     W1, W2, W3 = _w(Pd, bf16)
     F = (np.asarray(F, dtype=np.float64) - Pd["mu"]) * Pd["isd"]
@@ -174,11 +177,12 @@ def warm_start(n, Y, scale):
     """R0 = 0 and a column-constant A0 built from the per-point predictions:
     at a fixed point of Eq. 3-4, a(k,k) = colp(k) and, for i != k,
     a(i,k) = min(0, r(k,k) + colp(k) - max(0, r(i,k))), which is
-    min(0, r(k,k) + a(k,k)) up to the i-th term; so
-        A0(i,k) = min(0, (r_hat_k + a_hat_k) * p)   (i != k),
-        A0(k,k) = max(0, a_hat_k * p)               (Eq. 4 is never negative)."""
+    min(0, r(k,k) + a(k,k)) up to the i-th term -- the network's first output;
+    so
+        A0(i,k) = min(0, c_hat_k * p)   (i != k),
+        A0(k,k) = max(0, a_hat_k * p)   (Eq. 4 is never negative)."""
     R0 = np.zeros((n, n))
-    c = np.minimum(0.0, (Y[:, 0] + Y[:, 1]) * scale)
+    c = np.minimum(0.0, Y[:, 0] * scale)
     A0 = np.tile(c, (n, 1))
     np.fill_diagonal(A0, np.maximum(0.0, Y[:, 1] * scale))
     return R0, A0

@@ -140,21 +140,19 @@ def run(batch, R=None, A=None, damping=0.9, max_iter=1000, conv_iter=15, ws=None
     return R, A, res, ev[0].elapsed_time(ev[1])
 
 
-def warm_start(batch, P, P16, gamma=1.0, R=None, A=None):
-    """R0 = 0 and the network's column-constant A0 for every problem (features,
-    forward pass and warm start per problem), A0 scaled by ``gamma``, into
-    (R, A) (allocated before the timed region when omitted).
-    Returns (R, A, device ms)."""
+def warm_start(batch, P, P16, gamma=1.0, R=None, A=None, ws=None):
+    """R0 = 0 and the network's column-constant A0 for every problem, A0
+    scaled by ``gamma``: features, forward pass and warm start of the whole
+    batch in one library call, into (R, A) (allocated, like the workspace,
+    before the timed region when omitted).  Returns (R, A, device ms)."""
     R = torch.empty_like(batch.S) if R is None else R
     A = torch.empty_like(batch.S) if A is None else A
+    if ws is None:
+        ws = capi.apl_warm_start_batched_workspace(batch.n, batch.S.device)
+    scale = [batch.scale(b) * gamma for b in range(batch.count)]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
-    for b in range(batch.count):
-        sc = batch.scale(b)
-        F = capi.apl_features(batch.S_of(b), sc)
-        Y = capi.apl_forward(P, P16, F)
-        capi.apl_warm_start(Y, sc * gamma, view(R, batch.off, batch.n, batch.ld, b),
-                            view(A, batch.off, batch.n, batch.ld, b))
+    capi.apl_warm_start_batched(batch.S, R, A, batch.off, batch.n, batch.ld, scale, P, P16, ws=ws)
     ev[1].record()
     torch.cuda.synchronize()
     return R, A, ev[0].elapsed_time(ev[1])
@@ -171,9 +169,8 @@ def netsims(batch, R, A):
 
 
 def judge(cold, warm, tol=0.005):
-    """Per problem: keep the warm result when its net similarity is within
-    ``tol`` (relative) of the cold start's, else fall back to the cold one."""
-    keep = []
-    for (nc, ec), (nw, ew) in zip(cold, warm):
-        keep.append(ew > 0 and abs(nw - nc) <= tol * abs(nc))
-    return keep
+    """Per problem: keep the warm result when it has exemplars and its net
+    similarity is within ``tol`` (relative) of the cold start's (the
+    library's apl_judge), else fall back to the cold one."""
+    keep = capi.apl_judge([nc for nc, _ in cold], [nw for nw, _ in warm], tol)
+    return [k and ew > 0 for k, (_, ew) in zip(keep, warm)]

@@ -171,6 +171,11 @@ _SIGNATURES = {
     "apl_train_step": (C.c_int32, [_P, _P, _P, _P, C.c_int64, C.c_float, _P, _P, _I64, _P, _P,
                                    _P, _SZ, _P]),
     "apl_warm_start": (C.c_int32, [_P, _I64, C.c_float, _P, _P, _I64, _P]),
+    "apl_warm_start_batched_workspace_size": (_SZ, [_P, C.c_int32]),
+    "apl_warm_start_batched": (C.c_int32, [_P, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P, _P, _P,
+                                           _SZ, _P]),
+    "apl_set_standardisation": (C.c_int32, [_P, _P, _I64, _P]),
+    "apl_judge": (C.c_int32, [_P, _P, C.c_int32, C.c_double, _P]),
     "apl_ap_run_workspace_size": (_SZ, [_I64, _I64]),
     "apl_ap_run": (C.c_int32, [_P, _I64, _I64, _P, _P, C.c_float, C.POINTER(ApParams), C.c_int32,
                                _P, _P, _P, C.POINTER(AplResult), _P, _SZ, _P]),
@@ -700,3 +705,41 @@ def apl_ap_run(S, P, P16, scale, damping=0.9, max_iter=1000, conv_iter=15, judge
 def ap_wait_selftest(spin_limit=1 << 16, stream=None):
     """Status of the library's bounded-wait self-test (AP_ERR_TIMEOUT expected)."""
     return int(lib().ap_wait_selftest(int(spin_limit), _stream(stream)))
+
+
+def apl_warm_start_batched_workspace(n, device):
+    """A workspace for apl_warm_start_batched on problems of sizes n."""
+    return workspace(lib().apl_warm_start_batched_workspace_size(_i64_array(n), len(n)), device)
+
+
+def apl_warm_start_batched(S, R, A, offsets, n, ld, scale, P, P16, Y=None, ws=None, stream=None):
+    """Features, forward pass and column-constant warm start of every problem
+    of 1-D arenas (S, R, A) in one call; ``scale`` one float per problem."""
+    count = len(n)
+    sc = (C.c_float * count)(*[float(x) for x in scale])
+    if ws is None:
+        ws = apl_warm_start_batched_workspace(n, S.device)
+    _check("apl_warm_start_batched",
+           lib().apl_warm_start_batched(_ptr(S), _ptr(R), _ptr(A), _i64_array(offsets), _i64_array(n),
+                                        _i64_array(ld), count, sc, _ptr(P), _ptr(P16), _ptr(Y),
+                                        _ptr(ws), ws.numel(), _stream(stream)))
+    return R, A
+
+
+def apl_set_standardisation(P, F, stream=None):
+    """Writes the input standardisation of features F (rows x 25) into P."""
+    _check("apl_set_standardisation",
+           lib().apl_set_standardisation(_ptr(P), _ptr(F.contiguous()), F.shape[0], _stream(stream)))
+
+
+def apl_judge(cold_netsim, warm_netsim, tol=0.005):
+    """Per problem: True when the warm net similarity is within ``tol`` of the
+    cold one (the library's judge)."""
+    count = len(cold_netsim)
+    c = (C.c_double * count)(*[float(x) for x in cold_netsim])
+    w = (C.c_double * count)(*[float(x) for x in warm_netsim])
+    out = (C.c_int32 * count)()
+    k = lib().apl_judge(c, w, count, float(tol), out)
+    if k < 0:
+        raise ApgbError("apl_judge", k)
+    return [bool(x) for x in out]

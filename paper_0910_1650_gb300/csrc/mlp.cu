@@ -13,9 +13,11 @@
 //         0-15), with D = feature 20: positive where k is denser than all of
 //         its neighbours, as exemplars tend to be
 //   24    the fraction of those 16 neighbours with D(j) > D(k)
-// A 25-256-256-3 network (ReLU) maps them to (r_hat, a_hat, logit): predicted
-// converged r(k,k)/p, a(k,k)/p and the exemplar log-odds.  Training: mean over
-// rows of (r_hat-t_r)^2 + (a_hat-t_a)^2 + softplus(logit) - t_e*logit, Adam.
+// A 25-256-256-3 network (ReLU) maps them to (c_hat, a_hat, logit): the
+// predicted converged column value min(0, r(k,k) + a(k,k))/p that the warm
+// start writes into column k, a(k,k)/p and the exemplar log-odds.  Training:
+// mean over rows of (c_hat-t_c)^2 + (a_hat-t_a)^2 + softplus(logit) -
+// t_e*logit, Adam.
 //
 // Parameters: one flat fp32 vector (W1 256x25, b1, W2 256x256, b2, W3 3x256,
 // b3, mu 25, isd 25); the input is standardised first, x -> (x - mu) * isd,
@@ -27,6 +29,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -42,11 +45,12 @@ constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * IN, OFF_W2 = OFF_B1 + HID,
 // ---- features -------------------------------------------------------------------
 constexpr int TOPK = 16;
 
-// One block per row k (grid-stride): rows of S read once; per-thread sorted
-// top-16 (value, index) lists merged by 16 rounds of block arg-max ordered by
-// (value desc, index asc).  Writes features 0-22 and the 16 neighbour indices.
-__global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, float scale,
-                                float* F, int32_t* nbr) {
+// Rows k0, k0 + kstep, ... of one problem, one row per block at a time: rows
+// of S read once; per-thread sorted top-16 (value, index) lists merged by 16
+// rounds of block arg-max ordered by (value desc, index asc).  Writes
+// features 0-22 and the 16 neighbour indices (problem-local).
+__device__ __forceinline__ void features_rows(const float* __restrict__ S, int n, int64_t ld, float scale,
+                                              float* F, int32_t* nbr, int k0, int kstep) {
     __shared__ float hv[32];
     __shared__ int hi[32];
     __shared__ double s1w[32], s2w[32];
@@ -56,7 +60,7 @@ __global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, 
     float thr[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) thr[q] = -(scale * (0.125f * (float)(1 << q)));   // exact: powers of 2
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    for (int k = k0; k < n; k += kstep) {
         const float* row = S + (int64_t)k * ld;
         float top[TOPK];
         int topi[TOPK];
@@ -150,10 +154,13 @@ __global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, 
     }
 }
 
-// Features 23-24 from the densities of each point's 16 neighbours.
-__global__ void neighbour_density_kernel(int n, const int32_t* __restrict__ nbr, float* F) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+__global__ void features_kernel(const float* __restrict__ S, int n, int64_t ld, float scale,
+                                float* F, int32_t* nbr) {
+    features_rows(S, n, ld, scale, F, nbr, blockIdx.x, gridDim.x);
+}
+
+// Features 23-24 of row k from the densities of its 16 neighbours.
+__device__ __forceinline__ void neighbour_row(int k, const int32_t* __restrict__ nbr, float* F) {
     const float d = F[(int64_t)k * IN + F_DENS];
     float mx = -INFINITY;
     int denser = 0;
@@ -167,6 +174,50 @@ __global__ void neighbour_density_kernel(int n, const int32_t* __restrict__ nbr,
     F[(int64_t)k * IN + 24] = (float)denser * (1.f / TOPK);
 }
 
+__global__ void neighbour_density_kernel(int n, const int32_t* __restrict__ nbr, float* F) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) neighbour_row(k, nbr, F);
+}
+
+// ---- the same over a batch of problems (feature rows of problem b from frow) ----
+struct BatchProblem {
+    const float* S;         // the problem's S (row stride ld)
+    float *R, *A;           // its messages (row stride ld)
+    int64_t ld;
+    int64_t frow;           // first row of the problem in the feature / output arenas
+    int n;
+    float scale;
+    int b0, nb;             // feature blocks: [b0, b0 + nb)
+    int w0;                 // warm-start blocks: [w0, w0 + n), one per row
+    int pad;
+};
+
+// Largest b with key(P[b]) <= x (P sorted by key).
+template <class F>
+__device__ __forceinline__ int batch_problem_of(const BatchProblem* P, int count, int64_t x, F key) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (key(P[mid]) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void features_batched_kernel(const BatchProblem* __restrict__ P, int count, float* F, int32_t* nbr) {
+    const int b = batch_problem_of(P, count, blockIdx.x, [](const BatchProblem& q) { return (int64_t)q.b0; });
+    const BatchProblem& q = P[b];
+    features_rows(q.S, q.n, q.ld, q.scale, F + q.frow * IN, nbr + q.frow * TOPK, blockIdx.x - q.b0, q.nb);
+}
+
+__global__ void neighbour_density_batched_kernel(const BatchProblem* __restrict__ P, int count, int64_t rows,
+                                                 const int32_t* __restrict__ nbr, float* F) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= rows) return;
+    const int b = batch_problem_of(P, count, t, [](const BatchProblem& q) { return q.frow; });
+    const BatchProblem& q = P[b];
+    neighbour_row((int)(t - q.frow), nbr + q.frow * TOPK, F + q.frow * IN);
+}
+
 // Fn = (F - mu) * isd, row-major [rows x IN].
 __global__ void standardise_kernel(const float* __restrict__ F, int rows,
                                    const float* __restrict__ P, float* Fn) {
@@ -174,6 +225,36 @@ __global__ void standardise_kernel(const float* __restrict__ F, int rows,
     if (e >= (int64_t)rows * IN) return;
     const int j = (int)(e % IN);
     Fn[e] = (F[e] - P[OFF_MU + j]) * P[OFF_ISD + j];
+}
+
+// Column j of the standardisation from F [rows x IN] (one block per column,
+// float64 sums in a fixed order): mu = mean, isd = 1 / max(std, 1e-3) with the
+// population standard deviation.
+__global__ void standardisation_kernel(const float* __restrict__ F, int64_t rows, float* P) {
+    __shared__ double s1[256], s2[256];
+    const int j = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double v = (double)F[r * IN + j];
+        a += v;
+        b += v * v;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double m = s1[0] / (double)rows;
+        const double var = fmax(0.0, s2[0] / (double)rows - m * m);
+        P[OFF_MU + j] = (float)m;
+        P[OFF_ISD + j] = (float)(1.0 / fmax(sqrt(var), 1e-3));
+    }
 }
 
 // ---- dense layers ----------------------------------------------------------------
@@ -368,22 +449,39 @@ __global__ void targets_kernel(const float* __restrict__ R, const float* __restr
                                float* T) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    T[k * 3 + 0] = R[(int64_t)k * ld + k] * inv_scale;
+    T[k * 3 + 0] = fminf(0.f, R[(int64_t)k * ld + k] + A[(int64_t)k * ld + k]) * inv_scale;
     T[k * 3 + 1] = A[(int64_t)k * ld + k] * inv_scale;
     T[k * 3 + 2] = dec[k] == k ? 1.f : 0.f;
 }
 
 // Column-constant availabilities from the per-point predictions (the fixed
-// point of Eq. 3-4 up to the i-th term): A(i,k) = min(0, (r_hat_k+a_hat_k)p)
-// for i != k, A(k,k) = max(0, a_hat_k p).  One block-row of A per block.
+// point of Eq. 3-4 up to the i-th term): A(i,k) = min(0, c_hat_k p) for
+// i != k, A(k,k) = max(0, a_hat_k p).  One block-row of A per block.
 __global__ void warm_columns_kernel(const float* __restrict__ Y, int n, float scale, float* A,
                                     int64_t ld) {
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         float* row = A + (int64_t)i * ld;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const float rh = Y[k * 3 + 0], ah = Y[k * 3 + 1];
-            row[k] = (k == i) ? fmaxf(0.f, ah * scale) : fminf(0.f, (rh + ah) * scale);
+            const float ch = Y[k * 3 + 0], ah = Y[k * 3 + 1];
+            row[k] = (k == i) ? fmaxf(0.f, ah * scale) : fminf(0.f, ch * scale);
         }
+    }
+}
+
+// The warm start of every problem of a batch: one block per row i of problem
+// b; R(i,:) = 0 and A(i,:) the column-constant availabilities of b's
+// predictions (as warm_columns_kernel).
+__global__ void warm_batched_kernel(const BatchProblem* __restrict__ P, int count, const float* __restrict__ Y) {
+    const int b = batch_problem_of(P, count, blockIdx.x, [](const BatchProblem& q) { return (int64_t)q.w0; });
+    const BatchProblem& q = P[b];
+    const int i = blockIdx.x - q.w0;
+    const float* y = Y + q.frow * OUT;
+    float* rr = q.R + (int64_t)i * q.ld;
+    float* ar = q.A + (int64_t)i * q.ld;
+    for (int k = threadIdx.x; k < q.n; k += blockDim.x) {
+        const float ch = y[k * 3 + 0], ah = y[k * 3 + 1];
+        rr[k] = 0.f;
+        ar[k] = (k == i) ? fmaxf(0.f, ah * q.scale) : fminf(0.f, ch * q.scale);
     }
 }
 
@@ -651,4 +749,118 @@ APGB_API int32_t apl_ap_run(const float* S, int64_t n, int64_t ld, const float* 
     out->warm_ms = ms[2];
     out->cold_ms = ms[3];
     return out->result.status;
+}
+
+// ---- the learned warm start over a batch of problems ------------------------------------
+namespace apgb {
+namespace mlp {
+
+constexpr int64_t kFwdChunk = 65536;     // rows per forward pass (bounds the layer scratch)
+
+static size_t carve_batch(void* ws, const int64_t* n, int32_t count, BatchProblem** table, float** F,
+                          int32_t** nbr, float** Y, void** mlp_ws, size_t* mlp_bytes) {
+    int64_t rows = 0;
+    for (int32_t b = 0; b < count; ++b) rows += n[b];
+    MlpWs tmp;
+    const size_t mb = carve(nullptr, std::min(rows, kFwdChunk), &tmp);
+    Carver c(ws);
+    BatchProblem* t = c.take<BatchProblem>((size_t)count);
+    float* f = c.take<float>((size_t)rows * IN);
+    int32_t* nb = c.take<int32_t>((size_t)rows * TOPK);
+    float* y = c.take<float>((size_t)rows * OUT);
+    void* m = c.take<char>(mb);
+    if (table) *table = t;
+    if (F) *F = f;
+    if (nbr) *nbr = nb;
+    if (Y) *Y = y;
+    if (mlp_ws) *mlp_ws = m;
+    if (mlp_bytes) *mlp_bytes = mb;
+    return c.used;
+}
+
+}  // namespace mlp
+}  // namespace apgb
+
+APGB_API size_t apl_warm_start_batched_workspace_size(const int64_t* n, int32_t count) {
+    if (!n || count < 1) return 0;
+    for (int32_t b = 0; b < count; ++b)
+        if (n[b] < 2 || n[b] > INT_MAX) return 0;
+    return carve_batch(nullptr, n, count, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+APGB_API int32_t apl_warm_start_batched(const float* S, float* R, float* A, const int64_t* offsets,
+                                        const int64_t* n, const int64_t* ld, int32_t count,
+                                        const float* scale, const float* P, const void* P16, float* Y,
+                                        void* ws, size_t ws_bytes, void* stream) {
+    if (!S || !R || !A || !offsets || !n || !ld || !scale || !P || !P16 || count < 1)
+        return AP_ERR_INVALID_ARG;
+    const size_t need = apl_warm_start_batched_workspace_size(n, count);
+    if (!need) return AP_ERR_INVALID_ARG;
+    int64_t rows = 0, blocks = 0;
+    std::vector<BatchProblem> host(count);
+    for (int32_t b = 0; b < count; ++b) {
+        if (ld[b] < n[b] || offsets[b] < 0 || !(scale[b] > 0.f)) return AP_ERR_INVALID_ARG;
+        BatchProblem& q = host[b];
+        q.S = S + offsets[b];
+        q.R = R + offsets[b];
+        q.A = A + offsets[b];
+        q.ld = ld[b];
+        q.frow = rows;
+        q.n = (int)n[b];
+        q.scale = scale[b];
+        q.nb = (int)std::min<int64_t>(n[b], 1024);
+        q.b0 = (int)blocks;
+        blocks += q.nb;
+        rows += n[b];
+    }
+    if (blocks > INT_MAX || rows > INT_MAX) return AP_ERR_INVALID_ARG;
+    int w0 = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        host[b].w0 = w0;
+        w0 += host[b].n;
+    }
+    AP_TRY(require_sm103());
+    AP_TRY(check_ws(ws, ws_bytes, need));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchProblem* table = nullptr;
+    float *F = nullptr, *Yw = nullptr;
+    int32_t* nbr = nullptr;
+    void* mws = nullptr;
+    size_t mbytes = 0;
+    carve_batch(ws, n, count, &table, &F, &nbr, &Yw, &mws, &mbytes);
+    if (!Y) Y = Yw;
+    AP_CUDA_TRY(cudaMemcpyAsync(table, host.data(), sizeof(BatchProblem) * count, cudaMemcpyHostToDevice, s));
+    features_batched_kernel<<<(int)blocks, 256, 0, s>>>(table, count, F, nbr);
+    neighbour_density_batched_kernel<<<(int)((rows + 255) / 256), 256, 0, s>>>(table, count, rows, nbr, F);
+    note_launches(2);
+    AP_TRY(last_error());
+    MlpWs w;
+    carve(mws, std::min(rows, kFwdChunk), &w);
+    for (int64_t lo = 0; lo < rows; lo += kFwdChunk) {
+        const int cnt = (int)std::min(kFwdChunk, rows - lo);
+        AP_TRY(forward(P, static_cast<const __nv_bfloat16*>(P16), F + lo * IN, cnt, w, Y + lo * OUT, s));
+    }
+    warm_batched_kernel<<<w0, 256, 0, s>>>(table, count, Y);
+    note_launches(1);
+    return last_error();
+}
+
+APGB_API int32_t apl_set_standardisation(float* P, const float* F, int64_t rows, void* stream) {
+    if (!P || !F || rows < 1) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    standardisation_kernel<<<IN, 256, 0, static_cast<cudaStream_t>(stream)>>>(F, rows, P);
+    note_launches(1);
+    return last_error();
+}
+
+APGB_API int32_t apl_judge(const double* cold_netsim, const double* warm_netsim, int32_t count,
+                           double tol, int32_t* use_warm) {
+    if (!cold_netsim || !warm_netsim || !use_warm || count < 0 || !(tol >= 0.0)) return AP_ERR_INVALID_ARG;
+    int32_t kept = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        const double c = cold_netsim[b], w = warm_netsim[b];
+        use_warm[b] = (std::isfinite(c) && std::isfinite(w) && std::fabs(w - c) <= tol * std::fabs(c)) ? 1 : 0;
+        kept += use_warm[b];
+    }
+    return kept;
 }

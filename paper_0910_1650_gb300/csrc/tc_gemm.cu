@@ -504,9 +504,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const bool full_tile = col_half + 128 <= p.N;
                     uint32_t ra[32], rb[32];
                     // TOP2 also keeps the runner-up (the best of the other columns,
-                    // lowest column on ties); columns arrive in increasing order
+                    // lowest column on ties); columns arrive in increasing order.
                     auto scan = [&](uint32_t (&v)[32], int c, auto top2) {
                         const int kcol = col_half + c * OUT_COLS;
+                        const bool ragged = !full_tile && kcol + OUT_COLS > p.N;
 #pragma unroll
                         for (int u4 = 0; u4 < 8; ++u4) {
                             const float4 b4 = __ldg(reinterpret_cast<const float4*>(bn + c * OUT_COLS) + u4);
@@ -517,18 +518,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                                                          make_float2(__uint_as_float(v[4 * u4 + 2]),
                                                                      __uint_as_float(v[4 * u4 + 3])));
                             float sc[4] = {lo.x, lo.y, hi.x, hi.y};
+                            if (ragged) {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    if (kcol + 4 * u4 + e >= p.N) sc[e] = -INFINITY;
+                            }
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int k = kcol + 4 * u4 + e;
-                                if (!full_tile && k >= p.N) sc[e] = -INFINITY;
                                 if (decltype(top2)::value) {
-                                    if (sc[e] > best) {
-                                        best2 = best; bidx2 = bidx; best = sc[e]; bidx = k;
-                                    } else if (sc[e] > best2) {
-                                        best2 = sc[e]; bidx2 = k;
-                                    }
+                                    const bool gt = sc[e] > best, gt2 = sc[e] > best2;
+                                    bidx2 = gt ? bidx : (gt2 ? k : bidx2);
+                                    best2 = fmaxf(best2, fminf(sc[e], best));
+                                    bidx = gt ? k : bidx;
+                                    best = fmaxf(best, sc[e]);
                                 } else if (sc[e] > best) {
-                                    best = sc[e]; bidx = k;
+                                    best = sc[e];
+                                    bidx = k;
                                 }
                             }
                         }

@@ -33,9 +33,7 @@ def train(F, T, epochs=30, batch=4096, lr=1e-3, seed=synth.SEED_BASE + 77, shuff
     """Adam on (F, T) with the library's train step; minibatches follow a
     seeded permutation fixed per epoch.  Returns (P, P16, per-epoch mean loss)."""
     P = torch.from_numpy(synth.mlp_init(seed)).cuda()
-    n_in = F.shape[1]
-    P[-2 * n_in:-n_in] = F.mean(dim=0)                       # fixed input standardisation
-    P[-n_in:] = 1.0 / F.std(dim=0, unbiased=False).clamp_min(1e-3)
+    capi.apl_set_standardisation(P, F)                       # fixed input standardisation
     P16 = torch.empty(P.numel(), dtype=torch.bfloat16, device=P.device)
     capi.apl_sync_bf16(P, P16)
     M = torch.zeros_like(P)

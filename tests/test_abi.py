@@ -41,3 +41,13 @@ def test_workspace_queries_without_gpu(lib):
 def test_struct_layout():
     assert ctypes.sizeof(capi.ApParams) == 20
     assert ctypes.sizeof(capi.ApResult) == 56
+
+
+def test_judge_is_the_half_percent_rule():
+    """apl_judge (host only): keep the warm result exactly when its net
+    similarity is within tol of the cold one's, both finite."""
+    from paper_0910_1650_gb300 import capi
+    cold = [-100.0, -100.0, -100.0, -100.0, float("nan"), -50.0]
+    warm = [-100.5, -100.51, -99.5, -99.4, -100.0, float("inf")]
+    assert capi.apl_judge(cold, warm, 0.005) == [True, False, True, False, False, False]
+    assert capi.apl_judge([-1.0], [-1.0], 0.0) == [True]
