@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_POINTS, DIM = 20000, 64
+REFINE_ROUNDS = 8                 # Algorithm 3 Step 4's refinement rounds
 DAMPING, MAX_ITER, CONV_ITER = 0.9, 1000, 15
 METRIC = "AP sweep HBM GB/s vs peak; time-to-converge vs plain GPU AP at equal net sim"
 WORKLOAD = ("plain dense AP, N=20000, d=64, 50-Gaussian mixture (centres N(0,25I), sigma 1, "
@@ -562,6 +563,17 @@ def time_to_converge(dev):
     full["learned_landmarks"] = lap_learned(Xd)
     full["learned_landmarks"]["netsim_rel_vs_uniform"] = (
         (full["learned_landmarks"]["netsim"] - full["netsim"]) / abs(full["netsim"]))
+    # Algorithm 3 in full (Steps 1-4, Step 4 refining the merged centres) on all 1e6 points
+    (_, _, lf1), t_f1 = timed(lambda: capi.lap_run_full(Xd, 20000, 20000, seed=synth.config_seed(3),
+                                                        precision="bf16", damping=DAMPING,
+                                                        max_iter=MAX_ITER, conv_iter=CONV_ITER,
+                                                        refine_rounds=REFINE_ROUNDS), warm=False)
+    full["steps_1_4_refined"] = {"ms": round(t_f1, 1), "levels": lf1["levels"],
+                                 "unassigned": lf1["unassigned"], "exemplars_at": lf1["exemplars_at"],
+                                 "n_exemplars": lf1["n_exemplars"], "netsim": lf1["netsim"],
+                                 "refine": [lf1["refine_rounds"], lf1["refine_removed"],
+                                            lf1["refine_moved"]],
+                                 "netsim_rel_vs_steps_1_2": (lf1["netsim"] - full["netsim"]) / abs(full["netsim"])}
     del Xd
     m = 100000
     Xs = torch.from_numpy(X[:m]).to(dev)
@@ -575,9 +587,26 @@ def time_to_converge(dev):
                                                    precision="bf16", damping=DAMPING,
                                                    max_iter=MAX_ITER, conv_iter=CONV_ITER))
     lrn = lap_learned(Xs)
+    (_, _, lf0), t_full0 = timed(lambda: capi.lap_run_full(Xs, 20000, 20000, seed=synth.config_seed(3),
+                                                           precision="bf16", damping=DAMPING,
+                                                           max_iter=MAX_ITER, conv_iter=CONV_ITER))
     (_, _, lf), t_full = timed(lambda: capi.lap_run_full(Xs, 20000, 20000, seed=synth.config_seed(3),
                                                          precision="bf16", damping=DAMPING,
-                                                         max_iter=MAX_ITER, conv_iter=CONV_ITER))
+                                                         max_iter=MAX_ITER, conv_iter=CONV_ITER,
+                                                         refine_rounds=REFINE_ROUNDS))
+    # landmark count against net similarity (Table 1's trend), Steps 1-4 refined:
+    # the smallest count within 0.5 % of plain AP is the equal-netsim point
+    lsweep = []
+    for L in (2000, 5000, 10000, 20000):
+        (_, _, lq), t_q = timed(lambda: capi.lap_run_full(Xs, L, L, seed=synth.config_seed(3),
+                                                          precision="bf16", damping=DAMPING,
+                                                          max_iter=MAX_ITER, conv_iter=CONV_ITER,
+                                                          refine_rounds=REFINE_ROUNDS), warm=False)
+        lsweep.append({"landmarks": L, "ms": round(t_q, 1), "n_exemplars": lq["n_exemplars"],
+                       "levels": lq["levels"],
+                       "netsim_rel_diff": (lq["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
+                       "time_ratio_plain_over_lap": round(t_plain / t_q, 3)})
+    equal = [q for q in lsweep if abs(q["netsim_rel_diff"]) <= 0.005]
     out["lap"] = {
         "workload": "1000 Gaussians in R^128 (sigma 0.5, centres N(0,16I)); 20000 uniform landmarks; "
                     "learned: the 20000 best exemplar scores of a 40000-point uniform pool",
@@ -586,8 +615,16 @@ def time_to_converge(dev):
         "lap_steps_1_4": {"ms": round(t_full, 1), "levels": lf["levels"], "base_case": lf["base_case"],
                           "unassigned": lf["unassigned"], "exemplars_at": lf["exemplars_at"],
                           "n_exemplars": lf["n_exemplars"], "netsim": lf["netsim"],
+                          "refine": {"rounds": lf["refine_rounds"], "removed": lf["refine_removed"],
+                                     "moved": lf["refine_moved"]},
                           "time_ratio_plain_over_lap": round(t_plain / t_full, 3),
-                          "netsim_rel_diff": (lf["netsim"] - exp_["netsim"]) / abs(exp_["netsim"])},
+                          "netsim_rel_diff": (lf["netsim"] - exp_["netsim"]) / abs(exp_["netsim"]),
+                          "without_refinement": {
+                              "ms": round(t_full0, 1), "n_exemplars": lf0["n_exemplars"],
+                              "netsim_rel_diff": (lf0["netsim"] - exp_["netsim"]) / abs(exp_["netsim"])}},
+        "landmark_sweep_steps_1_4": lsweep,
+        "equal_netsim": (dict(equal[0], rule="smallest landmark count with |netsim - plain| <= 0.5 %")
+                         if equal else None),
         "lap_learned": dict(lrn, time_ratio_plain_over_lap=round(t_plain / lrn["ms"], 3),
                             netsim_rel_diff=(lrn["netsim"] - exp_["netsim"]) / abs(exp_["netsim"])),
         "full_1e6": full,

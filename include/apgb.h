@@ -504,6 +504,53 @@ int32_t   apl_ap_run(const float* S, int64_t n, int64_t ld, const float* P, cons
                      int32_t* idx, apl_result* out, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Row shards: Algorithm 1 (Section 2) with the rows of S, R and A split
+ * between devices (the O(N^2) cost per iteration that Section 3 states is
+ * divided by the shard count).  Given the column vectors colp(k) = sum over
+ * i' != k of max(0, r(i',k)) and r(k,k), both halves of an iteration are
+ * row-local (Eq. 2 needs row i only; Eq. 3-4 need row i, colp and r(k,k)),
+ * so each shard sweeps its own rows and the shards exchange, once per
+ * iteration, their shares of those two vectors and of the decision counts:
+ *
+ *   ap_shard_begin                     once
+ *   repeat:
+ *     ap_shard_sweep(..., red)         one fused sweep over the shard's rows;
+ *                                      red <- its shares
+ *     red <- sum of red over shards    (the caller's all-reduce: 2n+2 floats)
+ *     ap_shard_finish(..., red, &done) c = r(k,k) + colp; stop rule
+ *   until done
+ *
+ * Every shard applies the stop rule to the same totals, so all stop
+ * together.  One shard holding every row is Algorithm 1 on one device.
+ *  S, R, A     device float32: the shard's rows r0 .. r1-1 of the n x n
+ *              matrices, (r1 - r0) x ld each, row j holding global row r0+j
+ *              (ld >= n, ld % 4 == 0, 16-byte aligned).  R, A: the initial
+ *              messages in, the final ones out (as ap_iterate).
+ *  decisions   device int32 [r1 - r0] out or NULL: each row's decision.
+ *  red         device float [2n + 2]: (colp share [n], r(k,k) share [n] --
+ *              zero off the shard's rows --, exemplar-set changes, exemplars);
+ *              ap_shard_sweep writes it, the caller replaces it by its sum
+ *              over the shards, ap_shard_finish reads it.
+ *  done        host: 1 once the run has stopped; then R holds the final
+ *              responsibilities and out (host, may be NULL) iters/converged.
+ *  ws          ap_shard_workspace_size(n, ld, r0, r1) bytes, kept across the
+ *              calls of one run (it holds the iteration state).  The same
+ *              leading arguments go to all three calls.
+ *  ap_shard_begin checks the shard's rows for NaN/Inf (AP_ERR_NONFINITE) and
+ *  synchronises; ap_shard_sweep only enqueues; ap_shard_finish synchronises.
+ * ------------------------------------------------------------------------- */
+size_t    ap_shard_workspace_size(int64_t n, int64_t ld, int64_t r0, int64_t r1);
+int32_t   ap_shard_begin(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                         int64_t r1, const ap_params* params, int32_t* decisions, void* ws,
+                         size_t ws_bytes, void* stream);
+int32_t   ap_shard_sweep(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                         int64_t r1, const ap_params* params, int32_t* decisions, float* red,
+                         void* ws, size_t ws_bytes, void* stream);
+int32_t   ap_shard_finish(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                          int64_t r1, const ap_params* params, int32_t* decisions, const float* red,
+                          int32_t* done, ap_result* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Launch configuration of the ap_iterate sweep, and its autotuner.
  *
  * A cluster of `cluster` CTAs spans one row; each CTA owns a slice of the

@@ -179,6 +179,13 @@ _SIGNATURES = {
     "apl_ap_run_workspace_size": (_SZ, [_I64, _I64]),
     "apl_ap_run": (C.c_int32, [_P, _I64, _I64, _P, _P, C.c_float, C.POINTER(ApParams), C.c_int32,
                                _P, _P, _P, C.POINTER(AplResult), _P, _SZ, _P]),
+    "ap_shard_workspace_size": (_SZ, [_I64, _I64, _I64, _I64]),
+    "ap_shard_begin": (C.c_int32, [_P, _P, _P, _I64, _I64, _I64, _I64, C.POINTER(ApParams), _P, _P,
+                                   _SZ, _P]),
+    "ap_shard_sweep": (C.c_int32, [_P, _P, _P, _I64, _I64, _I64, _I64, C.POINTER(ApParams), _P, _P,
+                                   _P, _SZ, _P]),
+    "ap_shard_finish": (C.c_int32, [_P, _P, _P, _I64, _I64, _I64, _I64, C.POINTER(ApParams), _P, _P,
+                                    _P, C.POINTER(ApResult), _P, _SZ, _P]),
     "ap_sweep_get_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_set_config": (C.c_int32, [_I64, C.POINTER(ApSweepConfig)]),
     "ap_sweep_plan": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, _P,

@@ -615,6 +615,33 @@ sweep_kernel(SweepLaunch L) {
 // Grid: (ceil(n/32), problems).
 constexpr int kFinCols = 32, kFinLanes = 8;
 
+// Step 4 of Algorithm 1 after launch t (one thread): the exemplar set of
+// iteration t-1 extends or resets the run of unchanged sets; stop once it
+// has been the same, and non-empty, for conv_iter iterations, or after
+// max_iter iterations.
+__device__ __forceinline__ void apply_stop_rule(SweepState* st) {
+    if (st->done) return;
+    const int t = st->t;
+    if (t >= 2) {
+        const int it = t - 1;
+        st->stable = (it == 1 || st->changes != 0) ? 1 : st->stable + 1;
+        if (st->conv_iter > 0 && st->stable >= st->conv_iter && st->n_ex > 0) {
+            st->done = 1;
+            st->converged = 1;
+            st->iters = it;
+            st->final_buf = it & 1;
+        }
+    }
+    if (!st->done && t == st->max_iter + 1) {
+        st->done = 1;
+        st->iters = st->max_iter;
+        st->final_buf = st->max_iter & 1;
+    }
+    st->changes = 0;
+    st->n_ex = 0;
+    st->t = t + 1;
+}
+
 __global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const SweepArgs* __restrict__ table) {
     const SweepArgs& a = table[blockIdx.y];
     const int cx = threadIdx.x % kFinCols, gy = threadIdx.x / kFinCols;
@@ -635,28 +662,7 @@ __global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const Sw
         const_cast<float*>(a.colp)[k] = t;
         const_cast<float*>(a.cvec)[k] = a.rkk[k] + t;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (st->done) return;
-        const int t = st->t;
-        if (t >= 2) {
-            const int it = t - 1;
-            st->stable = (it == 1 || st->changes != 0) ? 1 : st->stable + 1;
-            if (st->conv_iter > 0 && st->stable >= st->conv_iter && st->n_ex > 0) {
-                st->done = 1;
-                st->converged = 1;
-                st->iters = it;
-                st->final_buf = it & 1;
-            }
-        }
-        if (!st->done && t == st->max_iter + 1) {
-            st->done = 1;
-            st->iters = st->max_iter;
-            st->final_buf = st->max_iter & 1;
-        }
-        st->changes = 0;
-        st->n_ex = 0;
-        st->t = t + 1;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) apply_stop_rule(st);
 }
 
 __global__ void sweep_init_kernel(const SweepArgs* __restrict__ table, int max_iter, int conv_iter) {
@@ -1572,4 +1578,236 @@ APGB_API int32_t ap_sweep_autotune(const float* S, float* R, float* A, int64_t n
     fill_public(best_c, best);
     best->ms_per_iter = (float)best_ms;
     return AP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Row shards: Algorithm 1 with the rows of S, R and A split between several
+// devices.  The responsibility half of an iteration and the availability
+// half are row-local given the column vectors colp and c = r(k,k) + colp; a
+// shard sweeps its own rows with the kernel above (its work list names only
+// its rows, and its buffers are addressed from where global row 0 would be),
+// exports its share of the column sums, its diagonal responsibilities and its
+// decision counts, and the caller sums those over the shards (one all-reduce
+// of 2n + 2 floats per iteration) before the stop rule is applied to the
+// totals, identically on every shard.
+// ---------------------------------------------------------------------------
+namespace apgb {
+
+// A shard's share of the column sums in the fixed order of finalize_kernel,
+// with its r(k,k) (zero off its rows) and its decision counts: red = (colp
+// share [n], r(k,k) share [n], exemplar-set changes, exemplars).
+__global__ void __launch_bounds__(kFinCols * kFinLanes) shard_reduce_kernel(const SweepArgs* __restrict__ table,
+                                                                           float* red) {
+    const SweepArgs& a = table[0];
+    const int cx = threadIdx.x % kFinCols, gy = threadIdx.x / kFinCols;
+    const int k = blockIdx.x * kFinCols + cx;
+    __shared__ float part[kFinLanes][kFinCols];
+    float s = 0.f;
+    if (k < a.n) {
+#pragma unroll 4
+        for (int g = gy; g < a.G; g += kFinLanes) s += a.pcol[(int64_t)g * a.pstride + k];
+    }
+    part[gy][cx] = s;
+    __syncthreads();
+    if (gy == 0 && k < a.n) {
+        red[k] = ((part[0][cx] + part[1][cx]) + (part[2][cx] + part[3][cx])) +
+                 ((part[4][cx] + part[5][cx]) + (part[6][cx] + part[7][cx]));
+        red[a.n + k] = a.rkk[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        red[2 * a.n] = (float)a.st->changes;
+        red[2 * a.n + 1] = (float)a.st->n_ex;
+    }
+}
+
+// The summed values back into the iteration: colp, c = r(k,k) + colp and the
+// stop rule on the total counts.
+__global__ void shard_finish_kernel(const SweepArgs* __restrict__ table, const float* __restrict__ red) {
+    const SweepArgs& a = table[0];
+    SweepState* st = a.st;
+    if (st->done) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < a.n) {
+        const_cast<float*>(a.colp)[k] = red[k];
+        const_cast<float*>(a.cvec)[k] = red[a.n + k] + red[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->changes = (int32_t)red[2 * a.n];
+        st->n_ex = (int32_t)red[2 * a.n + 1];
+        apply_stop_rule(st);
+    }
+}
+
+__global__ void shard_nonfinite_kernel(const float* __restrict__ S, int64_t m, int n, int64_t ld,
+                                       SweepState* st) {
+    int local = 0;
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x)
+        for (int k = threadIdx.x; k < n; k += blockDim.x)
+            if (!isfinite(S[i * ld + k])) ++local;
+    local = __reduce_add_sync(0xffffffffu, local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&st->nonfinite, local);
+}
+
+struct ShardWs {
+    SweepArgs* table;
+    Unit* units;
+    int* ubeg;
+    float* pool;
+    SweepState* st;
+    float *R1, *colp, *cvec, *rkk;
+    int32_t* eflag;
+};
+
+// The shard's launch configuration (chosen for rows of n columns) and its
+// work list: the interleaved units of its m rows, moved to global rows r0...
+static int32_t shard_plan(int64_t n, int64_t r0, int64_t r1, Plan* plan) {
+    AP_TRY(choose_config((int)n, &plan->c));
+    plan->nmax = (int)n;
+    const Problem rows{nullptr, nullptr, nullptr, r1 - r0, r1 - r0, nullptr};
+    std::vector<char> active(1, 1);
+    plan_units(&rows, 1, active, plan);
+    for (Unit& u : plan->units) u.first += (int)r0;
+    return AP_OK;
+}
+
+static size_t carve_shard(void* ws, int64_t n, int64_t ld, int64_t m, const Plan& plan, ShardWs* w) {
+    Carver cv(ws);
+    w->table = cv.take<SweepArgs>(1);
+    w->units = cv.take<Unit>(max_units(1, plan.c));
+    w->ubeg = cv.take<int>((size_t)std::max(plan.c.R, 1) + 1);
+    w->pool = cv.take<float>(max_units(1, plan.c) * (size_t)n);
+    w->st = cv.take<SweepState>(1);
+    w->R1 = cv.take<float>((size_t)m * ld);
+    w->colp = cv.take<float>(n);
+    w->cvec = cv.take<float>(n);
+    w->rkk = cv.take<float>(n);
+    w->eflag = cv.take<int32_t>(n);
+    return cv.used;
+}
+
+// The shard's problem table entry: buffers addressed from global row 0 (only
+// rows r0 .. r1-1 are ever touched).
+static SweepArgs shard_args(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                            const ap_params* p, int32_t* dec, const Plan& plan, const ShardWs& w) {
+    SweepArgs a{};
+    const int64_t back = r0 * ld;
+    a.S = S - back;
+    a.R0 = R - back;
+    a.R1 = w.R1 - back;
+    a.A = A - back;
+    a.ld = ld;
+    a.n = (int)n;
+    a.n4 = (int)((n + 3) / 4);
+    a.w4 = (a.n4 + plan.c.C - 1) / plan.c.C;
+    a.G = plan.G[0];
+    a.ns = plan.c.NS;
+    a.lam = p->damping;
+    a.spin_limit = 1u << 20;
+    a.cvec = w.cvec;
+    a.colp = w.colp;
+    a.pcol = w.pool;
+    a.pstride = n;
+    a.rkk = w.rkk;
+    a.eflag = w.eflag;
+    a.dec = dec ? dec - r0 : nullptr;
+    a.st = w.st;
+    return a;
+}
+
+static bool shard_args_ok(const float* S, const float* R, const float* A, int64_t n, int64_t ld,
+                          int64_t r0, int64_t r1) {
+    return S && R && A && n >= 2 && n <= INT_MAX / 4 && ld >= n && !(ld & 3) && r0 >= 0 && r1 > r0 &&
+           r1 <= n && aligned16(S) && aligned16(R) && aligned16(A);
+}
+
+}  // namespace apgb
+
+APGB_API size_t ap_shard_workspace_size(int64_t n, int64_t ld, int64_t r0, int64_t r1) {
+    if (n < 2 || n > INT_MAX / 4 || ld < n || r0 < 0 || r1 <= r0 || r1 > n) return 0;
+    Plan plan;
+    if (shard_plan(n, r0, r1, &plan) != AP_OK) return 0;
+    ShardWs w;
+    return carve_shard(nullptr, n, ld, r1 - r0, plan, &w);
+}
+
+APGB_API int32_t ap_shard_begin(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                                int64_t r1, const ap_params* params, int32_t* decisions, void* ws,
+                                size_t ws_bytes, void* stream) {
+    if (!shard_args_ok(S, R, A, n, ld, r0, r1) || !valid_params(params)) return AP_ERR_INVALID_ARG;
+    AP_TRY(require_sm103());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan plan;
+    AP_TRY(shard_plan(n, r0, r1, &plan));
+    ShardWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_shard(nullptr, n, ld, r1 - r0, plan, &w)));
+    carve_shard(ws, n, ld, r1 - r0, plan, &w);
+    const SweepArgs a = shard_args(S, R, A, n, ld, r0, params, decisions, plan, w);
+    AP_CUDA_TRY(cudaMemcpyAsync(w.table, &a, sizeof(SweepArgs), cudaMemcpyHostToDevice, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(w.units, plan.units.data(), sizeof(Unit) * plan.units.size(),
+                                cudaMemcpyHostToDevice, s));
+    AP_CUDA_TRY(cudaMemcpyAsync(w.ubeg, plan.ubeg.data(), sizeof(int) * plan.ubeg.size(),
+                                cudaMemcpyHostToDevice, s));
+    AP_CUDA_TRY(cudaMemsetAsync(w.rkk, 0, sizeof(float) * n, s));
+    sweep_init_kernel<<<dim3((unsigned)((n + 255) / 256), 1), 256, 0, s>>>(w.table, params->max_iter,
+                                                                           params->conv_iter);
+    shard_nonfinite_kernel<<<(int)std::min<int64_t>(r1 - r0, 1024), 256, 0, s>>>(S, r1 - r0, (int)n, ld, w.st);
+    note_launches(2);
+    AP_TRY(last_error());
+    SweepState h;
+    AP_CUDA_TRY(cudaMemcpyAsync(&h, w.st, sizeof(SweepState), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    return h.nonfinite ? AP_ERR_NONFINITE : AP_OK;
+}
+
+APGB_API int32_t ap_shard_sweep(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                                int64_t r1, const ap_params* params, int32_t* decisions, float* red,
+                                void* ws, size_t ws_bytes, void* stream) {
+    if (!shard_args_ok(S, R, A, n, ld, r0, r1) || !valid_params(params) || !red) return AP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan plan;
+    AP_TRY(shard_plan(n, r0, r1, &plan));
+    ShardWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_shard(nullptr, n, ld, r1 - r0, plan, &w)));
+    carve_shard(ws, n, ld, r1 - r0, plan, &w);
+    const SweepConfig& c = plan.c;
+    const SweepLaunch L{w.table, w.units, w.ubeg, 1, c.W4, c.NS};
+    AP_TRY(launch_sweep(c, plan.clusters, L, s));
+    shard_reduce_kernel<<<(unsigned)((n + kFinCols - 1) / kFinCols), kFinCols * kFinLanes, 0, s>>>(w.table, red);
+    note_launches(2);
+    return last_error();
+}
+
+APGB_API int32_t ap_shard_finish(const float* S, float* R, float* A, int64_t n, int64_t ld, int64_t r0,
+                                 int64_t r1, const ap_params* params, int32_t* decisions, const float* red,
+                                 int32_t* done, ap_result* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!shard_args_ok(S, R, A, n, ld, r0, r1) || !valid_params(params) || !red || !done)
+        return AP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Plan plan;
+    AP_TRY(shard_plan(n, r0, r1, &plan));
+    ShardWs w;
+    AP_TRY(check_ws(ws, ws_bytes, carve_shard(nullptr, n, ld, r1 - r0, plan, &w)));
+    carve_shard(ws, n, ld, r1 - r0, plan, &w);
+    shard_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.table, red);
+    note_launches(1);
+    AP_TRY(last_error());
+    SweepState h;
+    AP_CUDA_TRY(cudaMemcpyAsync(&h, w.st, sizeof(SweepState), cudaMemcpyDeviceToHost, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h.error) return AP_ERR_TIMEOUT;
+    *done = h.done;
+    if (!h.done) return AP_OK;
+    const int64_t m = r1 - r0;
+    if (h.final_buf == 1)
+        AP_CUDA_TRY(cudaMemcpy2DAsync(R, ld * sizeof(float), w.R1, ld * sizeof(float), n * sizeof(float), m,
+                                      cudaMemcpyDeviceToDevice, s));
+    AP_CUDA_TRY(cudaStreamSynchronize(s));
+    const int32_t status = (params->conv_iter > 0 && !h.converged) ? AP_NOT_CONVERGED : AP_OK;
+    if (out) {
+        *out = ap_result{};
+        out->iters = h.iters;
+        out->converged = h.converged;
+        out->status = status;
+    }
+    return status;
 }
