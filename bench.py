@@ -309,6 +309,76 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_sharded(args):
+    """--sharded: the step's sweep (Algorithm 1 from zero messages to
+    convergence) on the same workload with the rows of S, R and A split over
+    the ranks, one GPU each, and one NCCL all-reduce of 2n + 2 floats per
+    iteration (sharded.iterate).  Total work is fixed as ranks are added
+    (strong scaling); with one rank it is the single-GPU sweep.  value =
+    20 B x N^2 x iterations over the slowest rank's device time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_0910_1650_gb300 import capi, sharded, synth
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    X, _ = synth.workload(1, scale=args.n / N_POINTS)
+    n = X.shape[0]
+    r0, r1 = sharded.row_range(n, world, rank)
+    S, _ = capi.ap_similarity(torch.from_numpy(X).to(dev), precision=args.precision)
+    ld = capi.padded_ld(n)
+    Sr = torch.zeros(r1 - r0, ld, dtype=torch.float32, device=dev)
+    Sr[:, :n] = S[r0:r1]
+    del S
+    torch.cuda.empty_cache()
+    R = torch.zeros_like(Sr)
+    A = torch.zeros_like(Sr)
+    sh = sharded.LibraryShard(Sr, R, A, n, r0, r1, damping=DAMPING, max_iter=MAX_ITER, conv_iter=CONV_ITER)
+    allreduce = sharded.torch_allreduce() if world > 1 else (lambda t: None)
+
+    def step():
+        R.zero_()
+        A.zero_()
+        return sharded.iterate(sh, allreduce)
+
+    for _ in range(args.warmup):
+        step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    iters = 0
+    ev0.record()
+    for _ in range(args.steps):
+        iters += step()["iters"]
+    ev1.record()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        value = 20.0 * n * n * iters / float(t.item()) / 1e9
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(float(t.item()) / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator; paper datasets unavailable)",
+            "config": {"workload": WORKLOAD, "n": n, "d": X.shape[1], "phase": "iterate to convergence",
+                       "iters_per_step": iters // max(args.steps, 1),
+                       "parallelism": f"rows of S, R, A split over {world} GPU(s), one all-reduce of "
+                                      f"2n+2 floats per iteration"}}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def small_problem(dev, reps=20):
     """The 500-point 2-D mixture (damping 0.5, max 200, 15 unchanged sweeps):
     S, R and A (1 MB each) stay in L2, so a run is bound by launch latency,
@@ -813,6 +883,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sharded", action="store_true",
+                    help="split the rows of S, R, A over the ranks (one all-reduce per iteration) "
+                         "and time the sweep to convergence")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -844,6 +917,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.sharded:
+        run_sharded(args)
     else:
         run_gpu(args)
 
