@@ -301,6 +301,7 @@ def run_gpu(args):
             del S, R, A, Xd
             torch.cuda.empty_cache()
             line["time_to_converge"] = time_to_converge(dev)
+            line["autotune"] = autotune(dev)
             line["small_problem"] = small_problem(dev)
             line["batch_learned"] = batch_learned(dev)
             line["paper_2d"] = paper_2d(dev)
@@ -377,6 +378,46 @@ def run_sharded(args):
                                       f"2n+2 floats per iteration"}}), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def autotune(dev, iters=30):
+    """The sweep autotuner on the step's workload (N = 20000): every admissible
+    (cluster, float4 per thread, stages) configuration timed over 10
+    iterations, the fastest pinned; reported against the built-in rule's
+    choice, each timed over ``iters`` iterations with per-launch CUDA events.
+    The pin is removed afterwards (the headline numbers use the rule)."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    X, _ = synth.workload(1)
+    n = X.shape[0]
+    S, _ = capi.ap_similarity(torch.from_numpy(X).to(dev), precision="bf16")
+    R = capi.empty_square(n, dev, 0.0)
+    A = capi.empty_square(n, dev, 0.0)
+
+    def per_iter():
+        R.zero_()
+        A.zero_()
+        _, _, r, _ = capi.ap_iterate(S, R, A, damping=DAMPING, max_iter=iters, conv_iter=0,
+                                     time_sweep=True, decisions=False)
+        return r["sweep_ms"] / r["sweep_launches"]
+
+    capi.ap_sweep_set_config(n)
+    rule = capi.ap_sweep_get_config(n)
+    per_iter()
+    t_rule = per_iter()
+    t0 = time.perf_counter()
+    best = capi.ap_sweep_autotune(S, R, A, damping=DAMPING, iters=10)
+    tune_s = time.perf_counter() - t0
+    t_best = per_iter()
+    capi.ap_sweep_set_config(n)
+    del S, R, A
+    torch.cuda.empty_cache()
+    cfg = lambda c: f"cluster {c['cluster']}, {c['ept']} float4/thread, {c['stages']} stages"
+    return {"n": n, "rule": cfg(rule), "rule_ms_per_iter": round(t_rule, 4),
+            "tuned": cfg(best), "tuned_ms_per_iter": round(t_best, 4), "tuning_s": round(tune_s, 2),
+            "rule_frac_of_tuned": round(t_best / t_rule, 4)}
 
 
 def small_problem(dev, reps=20):

@@ -29,12 +29,15 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <climits>
 #include <cmath>
 #include <functional>
 #include <map>
 #include <mutex>
+#include <set>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -712,10 +715,28 @@ static size_t sweep_smem(int w4, int ns, int C, int T) {
            (slots * (sizeof(Slot) + sizeof(int)) + 15) / 16 * 16;
 }
 
+// Every instantiation of the sweep kernel may use dynamic shared memory up to
+// the 227 KB opt-in limit and non-portable cluster sizes.  Set once per
+// device and instantiation (a launch still asks only for its own bytes), so
+// that launches of different configurations, also from several host threads,
+// never lower one another's ceiling.
+static int32_t prepare_sweep_fn(int ept) {
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> ready;
+    int dev = 0;
+    AP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (ready.count({dev, ept})) return AP_OK;
+    void* fn = sweep_ptr(ept);
+    AP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    AP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    ready.insert({dev, ept});
+    return AP_OK;
+}
+
 static int32_t max_clusters(int ept, int C, int T, size_t smem, int* out) {
     void* fn = sweep_ptr(ept);
-    AP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (C > 8) AP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    AP_TRY(prepare_sweep_fn(ept));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(T + 32, 1, 1);
@@ -1029,9 +1050,7 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
 
 static int32_t launch_sweep(const SweepConfig& c, int clusters, const SweepLaunch& L, cudaStream_t s,
                             bool set_attr = true) {
-    if (set_attr)
-        AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)c.smem));
+    if (set_attr) AP_TRY(prepare_sweep_fn(c.EPT));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.C * clusters, 1, 1);
     cfg.blockDim = dim3(c.T + 32, 1, 1);       // compute warps + the producer warp
@@ -1098,8 +1117,7 @@ static int32_t launch_chunk_graph(const SweepConfig& c, const Plan& plan, const 
     const GraphKey key{dev, L.table, L.count, c.C, c.EPT, c.NS, c.T, c.G, plan.clusters,
                        plan.nmax, c.smem, m};
     // the shared-memory ceiling is a function attribute, set outside the capture
-    AP_CUDA_TRY(cudaFuncSetAttribute(sweep_ptr(c.EPT), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)c.smem));
+    AP_TRY(prepare_sweep_fn(c.EPT));
     std::lock_guard<std::mutex> lock(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
@@ -1354,7 +1372,28 @@ struct SizeClass {
     std::vector<Problem> P;
     Plan plan;
     size_t ws_off = 0, ws_bytes = 0;
+    double work = 0.0;            // sum of n^2: the class's elements per iteration
 };
+
+// Library-owned streams on which ap_iterate_batched runs its size classes side
+// by side (created once per device).
+constexpr int kClassStreams = 4;
+static std::mutex g_cls_mu;
+static std::map<int, std::vector<cudaStream_t>> g_cls_streams;
+
+static int32_t class_streams(std::vector<cudaStream_t>* out) {
+    int dev = 0;
+    AP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_cls_mu);
+    auto it = g_cls_streams.find(dev);
+    if (it == g_cls_streams.end()) {
+        std::vector<cudaStream_t> v(kClassStreams);
+        for (auto& q : v) AP_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+        it = g_cls_streams.emplace(dev, v).first;
+    }
+    *out = it->second;
+    return AP_OK;
+}
 
 // The problems of each class, classes in increasing order of size (host only).
 static void split_classes(const Problem* P, int count, std::vector<std::vector<int>>* groups) {
@@ -1389,7 +1428,10 @@ static int32_t make_classes(const Problem* P, int count, std::vector<SizeClass>*
     for (const auto& idx : groups) {
         SizeClass c;
         c.idx = idx;
-        for (int b : idx) c.P.push_back(P[b]);
+        for (int b : idx) {
+            c.P.push_back(P[b]);
+            c.work += (double)P[b].n * (double)P[b].n;
+        }
         cls->push_back(std::move(c));
     }
     size_t at = 0;
@@ -1480,17 +1522,59 @@ APGB_API int32_t ap_iterate_batched(const float* S, float* R, float* A, const in
     size_t total = 0;
     AP_TRY(make_classes(P.data(), count, &cls, &total));
     AP_TRY(check_ws(ws, ws_bytes, total));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<std::vector<ap_result>> r(cls.size());
+    std::vector<int32_t> st(cls.size(), AP_OK);
+    auto run_class = [&](size_t i, cudaStream_t cs) {
+        r[i].assign(cls[i].P.size(), ap_result{});
+        st[i] = run_batch(cls[i].P.data(), (int)cls[i].P.size(), p, r[i].data(),
+                          static_cast<char*>(ws) + cls[i].ws_off, cls[i].ws_bytes, cs, cls[i].plan);
+    };
+    if (cls.size() == 1) {
+        run_class(0, s);
+    } else {
+        // classes run side by side, each on its own stream driven by its own
+        // host thread, largest work first: a class's tail (few problems
+        // left, clusters idle) overlaps the next classes' work.  Each class
+        // owns its workspace region, and a problem's results do not depend
+        // on what runs beside it.
+        std::vector<cudaStream_t> cs;
+        AP_TRY(class_streams(&cs));
+        const int workers = (int)std::min(cs.size(), cls.size());
+        std::vector<size_t> order(cls.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cls[a].work > cls[b].work; });
+        int dev = 0;
+        AP_CUDA_TRY(cudaGetDevice(&dev));
+        cudaEvent_t fork;
+        AP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        AP_CUDA_TRY(cudaEventRecord(fork, s));
+        for (int k = 0; k < workers; ++k) AP_CUDA_TRY(cudaStreamWaitEvent(cs[k], fork, 0));
+        cudaEventDestroy(fork);
+        std::atomic<size_t> next{0};
+        std::vector<std::thread> th;
+        for (int k = 0; k < workers; ++k)
+            th.emplace_back([&, k]() {
+                if (cudaSetDevice(dev) != cudaSuccess) return;
+                for (size_t j; (j = next.fetch_add(1)) < order.size();) run_class(order[j], cs[k]);
+            });
+        for (auto& t : th) t.join();
+        // join: the caller's stream continues after every class
+        for (int k = 0; k < workers; ++k) {
+            cudaEvent_t e;
+            AP_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            AP_CUDA_TRY(cudaEventRecord(e, cs[k]));
+            AP_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
+            cudaEventDestroy(e);
+        }
+        if (next.load() < order.size()) return AP_ERR_CUDA;    // a worker could not start
+    }
     int32_t worst = AP_OK;
-    std::vector<ap_result> r;
-    for (SizeClass& c : cls) {
-        r.assign(c.P.size(), ap_result{});
-        const int32_t st = run_batch(c.P.data(), (int)c.P.size(), p, r.data(),
-                                     static_cast<char*>(ws) + c.ws_off, c.ws_bytes,
-                                     static_cast<cudaStream_t>(stream), c.plan);
-        if (st < 0) return st;
-        worst = std::max(worst, st);
+    for (size_t i = 0; i < cls.size(); ++i) {
+        if (st[i] < 0) return st[i];
+        worst = std::max(worst, st[i]);
         if (out)
-            for (size_t j = 0; j < c.idx.size(); ++j) out[c.idx[j]] = r[j];
+            for (size_t j = 0; j < cls[i].idx.size(); ++j) out[cls[i].idx[j]] = r[i][j];
     }
     return worst;
 }

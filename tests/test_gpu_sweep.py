@@ -362,3 +362,40 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
     R, A, res, _ = capi.ap_iterate(dev_square(S), damping=0.5, max_iter=5, conv_iter=0)
     ref = oap.run(S, lam=0.5, fixed_iters=5)
     assert rel_inf(host(R), ref["R"]) <= TOL and rel_inf(host(A), ref["A"]) <= TOL
+
+
+def test_autotune_pins_a_configuration_that_matches_oracle_and_is_not_slower():
+    """ap_sweep_autotune times every admissible configuration and pins the
+    fastest: ap_sweep_get_config then reports it, iterations under it give
+    the oracle's messages, and it is no slower than the built-in rule (within
+    timing noise)."""
+    X, _ = synth.workload(1, scale=0.1)                  # 2000 points, 64-D
+    n = X.shape[0]
+    S = s32(X)
+    Sd = dev_square(S)
+    capi.ap_sweep_set_config(n)                          # start from the rule
+    try:
+        default = capi.ap_sweep_get_config(n)
+
+        def per_iter():
+            _, _, r, _ = capi.ap_iterate(Sd, damping=0.9, max_iter=40, conv_iter=0, time_sweep=True)
+            return r["sweep_ms"] / r["sweep_launches"]
+
+        per_iter()
+        t_default = min(per_iter() for _ in range(3))
+        best = capi.ap_sweep_autotune(Sd, damping=0.9, iters=10)
+        got = capi.ap_sweep_get_config(n)
+        assert (got["cluster"], got["ept"], got["stages"]) == (best["cluster"], best["ept"], best["stages"])
+        R, A, r, _ = capi.ap_iterate(Sd, damping=0.9, max_iter=20, conv_iter=0)
+        ref = oap.run(S, lam=0.9, fixed_iters=20)
+        Rg = R.cpu().numpy().astype(np.float64)
+        Ag = A.cpu().numpy().astype(np.float64)
+        assert np.abs(Rg - ref["R"]).max() <= 1e-4 * np.abs(ref["R"]).max()
+        assert np.abs(Ag - ref["A"]).max() <= 1e-4 * np.abs(ref["A"]).max()
+        t_tuned = min(per_iter() for _ in range(3))
+        print(f"\nautotune n={n}: default {default['cluster']}/{default['ept']}/{default['stages']} "
+              f"{t_default * 1e3:.1f} us, tuned {best['cluster']}/{best['ept']}/{best['stages']} "
+              f"{t_tuned * 1e3:.1f} us per iteration")
+        assert t_tuned <= 1.10 * t_default
+    finally:
+        capi.ap_sweep_set_config(n)
