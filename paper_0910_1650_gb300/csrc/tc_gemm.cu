@@ -503,11 +503,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const float* bn = p.bnrm + col_half;
                     const bool full_tile = col_half + 128 <= p.N;
                     uint32_t ra[32], rb[32];
-                    // TOP2 also keeps the runner-up (the best of the other columns,
-                    // lowest column on ties); columns arrive in increasing order.
+                    // ARGMAX: each 32-column chunk's maximum by a max tree, then, only
+                    // where it beats the running best, the chunk's first column
+                    // attaining it (lowest column on ties; chunks arrive in
+                    // increasing column order, so a strict compare keeps the
+                    // earlier chunk).  TOP2 also keeps the runner-up (the best of the
+                    // other columns, lowest column on ties), column by column.
                     auto scan = [&](uint32_t (&v)[32], int c, auto top2) {
                         const int kcol = col_half + c * OUT_COLS;
                         const bool ragged = !full_tile && kcol + OUT_COLS > p.N;
+                        float sc[32];
 #pragma unroll
                         for (int u4 = 0; u4 < 8; ++u4) {
                             const float4 b4 = __ldg(reinterpret_cast<const float4*>(bn + c * OUT_COLS) + u4);
@@ -517,25 +522,40 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const float2 hi = __ffma2_rn(mhalf, make_float2(b4.z, b4.w),
                                                          make_float2(__uint_as_float(v[4 * u4 + 2]),
                                                                      __uint_as_float(v[4 * u4 + 3])));
-                            float sc[4] = {lo.x, lo.y, hi.x, hi.y};
-                            if (ragged) {
+                            sc[4 * u4] = lo.x;
+                            sc[4 * u4 + 1] = lo.y;
+                            sc[4 * u4 + 2] = hi.x;
+                            sc[4 * u4 + 3] = hi.y;
+                        }
+                        if (ragged) {
 #pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    if (kcol + 4 * u4 + e >= p.N) sc[e] = -INFINITY;
+                            for (int e = 0; e < 32; ++e)
+                                if (kcol + e >= p.N) sc[e] = -INFINITY;
+                        }
+                        if (decltype(top2)::value) {
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const int k = kcol + e;
+                                const bool gt = sc[e] > best, gt2 = sc[e] > best2;
+                                bidx2 = gt ? bidx : (gt2 ? k : bidx2);
+                                best2 = fmaxf(best2, fminf(sc[e], best));
+                                bidx = gt ? k : bidx;
+                                best = fmaxf(best, sc[e]);
                             }
+                        } else {
+                            float t[16];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int k = kcol + 4 * u4 + e;
-                                if (decltype(top2)::value) {
-                                    const bool gt = sc[e] > best, gt2 = sc[e] > best2;
-                                    bidx2 = gt ? bidx : (gt2 ? k : bidx2);
-                                    best2 = fmaxf(best2, fminf(sc[e], best));
-                                    bidx = gt ? k : bidx;
-                                    best = fmaxf(best, sc[e]);
-                                } else if (sc[e] > best) {
-                                    best = sc[e];
-                                    bidx = k;
-                                }
+                            for (int e = 0; e < 16; ++e) t[e] = fmaxf(sc[2 * e], sc[2 * e + 1]);
+#pragma unroll
+                            for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                                for (int e = 0; e < w; ++e) t[e] = fmaxf(t[e], t[e + w]);
+                            if (t[0] > best) {
+                                int j = 31;
+#pragma unroll
+                                for (int e = 30; e >= 0; --e) j = (sc[e] == t[0]) ? e : j;
+                                best = t[0];
+                                bidx = kcol + j;
                             }
                         }
                         __syncwarp();                    // converged for the next tcgen05 op
