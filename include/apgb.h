@@ -87,6 +87,11 @@ typedef struct ap_params {
  * the sub-problems as well as A' (the paper carries availabilities only, so
  * R = 0 without this flag). */
 #define AP_FLAG_PAP_CARRY_R 4
+/* ap_params.flags: the caller has already checked this S for NaN/Inf (for
+ * example an earlier call on the same S, when a run is resumed in chunks);
+ * ap_iterate and ap_iterate_batched skip their own check, which reads S once
+ * more (4 bytes per element, a fifth of one iteration's traffic). */
+#define AP_FLAG_S_CHECKED 8
 
 /* Outputs of Algorithm 1 (Section 2): dpsim = sum of the data-point
  * similarities to their exemplars, expref = sum of the exemplars'

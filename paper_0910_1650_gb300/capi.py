@@ -25,6 +25,7 @@ AP_PREF_MEDIAN, AP_PREF_SCALAR, AP_PREF_VECTOR = 0, 1, 2
 AP_FLAG_TIME_SWEEP = 1
 AP_FLAG_NO_GRAPH = 2
 AP_FLAG_PAP_CARRY_R = 4
+AP_FLAG_S_CHECKED = 8
 AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
 AP_ERR_CAPACITY = -8
@@ -360,10 +361,11 @@ def ap_preference_median(S, stream=None):
 
 
 def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check_every=0,
-               time_sweep=False, decisions=True, graph=True, stream=None):
+               time_sweep=False, decisions=True, graph=True, s_checked=False, stream=None):
     """Runs Algorithm 1 in place on (R, A) (zeros when omitted).  ``graph``:
     enqueue each chunk of iterations as one CUDA graph (ignored with
-    ``time_sweep``).  Returns (R, A, result dict, decisions int32 tensor or None)."""
+    ``time_sweep``); ``s_checked``: S is known finite (skip the library's
+    NaN/Inf pass).  Returns (R, A, result dict, decisions int32 tensor or None)."""
     _dev_f32(S, "S")
     n = S.shape[0]
     if R is None:
@@ -376,7 +378,8 @@ def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check
         raise ValueError("S, R and A must share one leading dimension")
     dec = torch.empty(n, dtype=torch.int32, device=S.device) if decisions else None
     p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every),
-                 (AP_FLAG_TIME_SWEEP if time_sweep else 0) | (0 if graph else AP_FLAG_NO_GRAPH))
+                 (AP_FLAG_TIME_SWEEP if time_sweep else 0) | (0 if graph else AP_FLAG_NO_GRAPH)
+                 | (AP_FLAG_S_CHECKED if s_checked else 0))
     res = ApResult()
     ws = workspace(lib().ap_iterate_workspace_size(n, S.stride(0)), S.device)
     st = lib().ap_iterate(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),

@@ -1178,8 +1178,11 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     const dim3 col_grid((nmax + 255) / 256, count);
     const dim3 fin_grid((nmax + kFinCols - 1) / kFinCols, count);
     sweep_init_kernel<<<col_grid, 256, 0, s>>>(w.table, p->max_iter, p->conv_iter);
-    nonfinite_kernel<<<dim3(std::min(nmax, 1024), count), 256, 0, s>>>(w.table);
-    note_launches(2);
+    note_launches(1);
+    if (!(p->flags & AP_FLAG_S_CHECKED)) {
+        nonfinite_kernel<<<dim3(std::min(nmax, 1024), count), 256, 0, s>>>(w.table);
+        note_launches(1);
+    }
     AP_TRY(last_error());
     std::vector<SweepState> hs(count);
     auto read_states = [&]() -> int32_t {

@@ -232,7 +232,8 @@ def test_deterministic_bitwise():
 
 def test_resume_reproduces_uninterrupted_run():
     """Checkpoint/resume: 6 iterations then 5 from the saved (R, A) equal 11
-    straight iterations bitwise."""
+    straight iterations bitwise (the resumed call skips the NaN/Inf pass over
+    S that the first call made: AP_FLAG_S_CHECKED)."""
     S = dev_square(workload_S("mix64_2000"))
     R1, A1, _, _ = capi.ap_iterate(S, damping=0.9, max_iter=6, conv_iter=0)
     n = S.shape[0]
@@ -240,7 +241,7 @@ def test_resume_reproduces_uninterrupted_run():
     Ac = capi.empty_square(n, S.device)
     Rc.copy_(R1)
     Ac.copy_(A1)
-    R2, A2, _, _ = capi.ap_iterate(S, Rc, Ac, damping=0.9, max_iter=5, conv_iter=0)
+    R2, A2, _, _ = capi.ap_iterate(S, Rc, Ac, damping=0.9, max_iter=5, conv_iter=0, s_checked=True)
     R3, A3, _, _ = capi.ap_iterate(S, damping=0.9, max_iter=11, conv_iter=0)
     assert torch.equal(R2, R3) and torch.equal(A2, A3)
 
