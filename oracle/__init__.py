@@ -11,7 +11,8 @@ Modules:
   ap    -- Algorithm 1 (Eq. 1-4, damping, decisions, outputs) in two forms:
            the literal triple loop and the top-2 / column-sum form.
   pap   -- Algorithm 2 (partition, sub-runs, block-diagonal merge, warm start).
-  lap   -- Algorithm 3 Steps 1-2 (landmark AP, nearest-exemplar assignment).
+  lap   -- Algorithm 3: Steps 1-2 (landmark AP, nearest-exemplar assignment), Steps 1-4
+           (gate, recursion, merge) and Step 4's refinement of the centre set.
   mlp   -- the learned warm-start network (features, forward, backward, Adam).
   rng   -- splitmix64, restated independently of the CUDA path.
 
