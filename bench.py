@@ -302,6 +302,7 @@ def run_gpu(args):
             torch.cuda.empty_cache()
             line["time_to_converge"] = time_to_converge(dev)
             line["autotune"] = autotune(dev)
+            line["pap_table2"] = pap_table2(dev)
             line["small_problem"] = small_problem(dev)
             line["batch_learned"] = batch_learned(dev)
             line["paper_2d"] = paper_2d(dev)
@@ -378,6 +379,61 @@ def run_sharded(args):
                                       f"2n+2 floats per iteration"}}), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def pap_table2(dev, reps=5):
+    """Table 2's shape on a seeded stand-in: 2021 points in 62-D from 86
+    Gaussian classes (the faces' size, dimension and class count; centres
+    N(0, 4I), sigma 1), plain AP against PAP with k = 2, 4, 8, 16 equal
+    blocks, at the paper's damping 0.5 and at the workloads' 0.9; max 1000,
+    15 unchanged sweeps.  Iterations and device time of whole calls, means
+    over ``reps`` seeded sets."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ev[0].record()
+        r = fn()
+        ev[1].record()
+        ev[1].synchronize()
+        return r, ev[0].elapsed_time(ev[1])
+
+    out = {}
+    for lam in (0.5, 0.9):
+        kw = dict(damping=lam, max_iter=MAX_ITER, conv_iter=CONV_ITER)
+        rows = {"plain": [], **{k: [] for k in (2, 4, 8, 16)}}
+        for r in range(reps):
+            X, _ = synth.gaussian_mixture(2021, 62, 86, synth.SEED_BASE + 900 + r, 2.0, 1.0)
+            S, _ = capi.ap_similarity(torch.from_numpy(X).to(dev), precision="fp32")
+            (R, A, ra, _), t = timed(lambda: capi.ap_iterate(S, **kw))
+            _, ea = capi.ap_exemplars(S, R, A)
+            rows["plain"].append((ra["iters"], t, ea["netsim"], ea["n_exemplars"], ra["converged"]))
+            for k in (2, 4, 8, 16):
+                (_, _, _, pr), tp = timed(lambda: capi.pap_run(S, k, None, **kw))
+                f = pr["final"]
+                rows[k].append((f["iters"], tp, f["netsim"], f["n_exemplars"], f["converged"],
+                                pr["sub_iters_max"], ea["netsim"]))
+        plain = rows["plain"]
+        res = {"plain": {"iters": round(float(np.mean([x[0] for x in plain])), 1),
+                         "ms": round(float(np.mean([x[1] for x in plain])), 2),
+                         "converged": int(sum(x[4] for x in plain)),
+                         "n_exemplars": round(float(np.mean([x[3] for x in plain])), 1)}}
+        for k in (2, 4, 8, 16):
+            v = rows[k]
+            res[f"pap_k{k}"] = {
+                "step4_iters": round(float(np.mean([x[0] for x in v])), 1),
+                "step4_iters_over_plain": round(float(np.mean([x[0] for x in v])) / max(res["plain"]["iters"], 1), 3),
+                "sub_iters_max": round(float(np.mean([x[5] for x in v])), 1),
+                "ms": round(float(np.mean([x[1] for x in v])), 2),
+                "converged": int(sum(x[4] for x in v)),
+                "netsim_rel_diff_mean": float(np.mean([(x[2] - x[6]) / abs(x[6]) for x in v]))}
+        out[f"damping_{lam}"] = res
+    out["workload"] = ("2021 points, 62-D, 86 Gaussian classes (centres N(0,4I), sigma 1); equal "
+                       "contiguous blocks; %d seeded sets" % reps)
+    return out
 
 
 def autotune(dev, iters=30):
@@ -924,6 +980,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--pap-table2", action="store_true",
+                    help="only the PAP k sweep on Table 2's shape (prints one JSON line)")
     ap.add_argument("--sharded", action="store_true",
                     help="split the rows of S, R, A over the ranks (one all-reduce per iteration) "
                          "and time the sweep to convergence")
@@ -953,6 +1011,10 @@ def main():
         return
     if args.lap_only:
         lap_only(args)
+        return
+    if args.pap_table2:
+        import torch
+        print(json.dumps(pap_table2(torch.device("cuda", 0))), flush=True)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
