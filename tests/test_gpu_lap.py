@@ -310,3 +310,16 @@ def test_lap_full_refinement_raises_netsim_on_the_landmark_workload():
     assert E.size == r1["n_exemplars"]
     frac_clear, _ = _check_assignment(X, E, labels)
     assert frac_clear > 0.95
+
+
+def test_lap_refine_single_centre_only_moves_to_the_medoid():
+    """One centre: nothing can be dropped (no second centre), so the
+    refinement only moves the centre to the member nearest the mean of all
+    points; the oracle's choice, with every point labelled by it."""
+    X = _integer_clusters(8, k=1, per=40, d=8, spread=9)
+    E0 = np.array([3])
+    E_ref, hist = olap.refine(X, E0, -50.0, max_rounds=10)
+    E, idx, res = capi.lap_refine(torch.from_numpy(X).cuda(), torch.from_numpy(E0), -50.0, rounds=10)
+    assert np.array_equal(E.cpu().numpy(), E_ref) and E_ref.size == 1
+    assert res["removed"] == 0 and res["moved"] == sum(h["moved"] for h in hist)
+    assert np.all(idx.cpu().numpy() == E_ref[0])

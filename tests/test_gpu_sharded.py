@@ -98,3 +98,13 @@ def test_shard_rejects_non_finite_rows():
             assert e.value.status == -5                   # AP_ERR_NONFINITE
         else:
             sh.begin()
+
+
+def test_shards_of_an_odd_sized_problem():
+    """1001 points (not a multiple of 4: ragged float4 tail in every row)
+    over three shards of 334, 334 and 333 rows."""
+    X, _ = synth.gaussian_mixture(1001, 12, 9, 61, 5.0, 1.0)
+    S = oap.build_similarity(X)[0].astype(np.float32).astype(np.float64)
+    R, A, res = _run_shards(S, 3, damping=0.9, max_iter=25, conv_iter=0)
+    ref = oap.run(S, lam=0.9, fixed_iters=25)
+    assert _rel(R, ref["R"]) <= 1e-4 and _rel(A, ref["A"]) <= 1e-4
