@@ -794,6 +794,8 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
         nmax = std::max(nmax, n[b]);
         vec = vec && aligned16(S + soff[b]) && (lds[b] & 3) == 0;
     }
+    // the bf16 path's tensor stores need 16-byte aligned rows of S
+    if (precision != AP_PREC_FP32 && !vec) return AP_ERR_INVALID_ARG;
     AP_TRY(require_sm103());
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AP_TRY(check_ws(ws, ws_bytes, ap_similarity_batched_workspace_size(n, count, d)));
@@ -843,7 +845,6 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
             Sp[b] = host[b].S;
             rows = host[b].roff + host[b].npad;
         }
-        if (!vec) return AP_ERR_INVALID_ARG;         // TMA stores need aligned rows
         AP_TRY(tc_similarity_bf16_grouped(static_cast<const __nv_bfloat16*>(host[0].xc), host[0].nrm, rows,
                                           dpad, nn.data(), roffs.data(), Sp.data(), ld.data(), count,
                                           tables, err, s));
