@@ -68,11 +68,31 @@ struct Ctl {
     int abort;                      // any role gave up a bounded wait
 };
 
-// ARGMAX/TOP2: the second column half's per-row results, after Ctl.
+// ARGMAX/TOP2: the second column half's per-row results, after Ctl; the
+// staged column norms follow (16-byte aligned).
 struct Slots {
     float b1[BM], b2[BM];
     int j1[BM], j2[BM];
 };
+static_assert((sizeof(Ctl) + sizeof(Slots)) % 16 == 0, "norm table alignment");
+
+// Largest of three (sm_100 and later: one instruction).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// r[e] = take ? v[e] : r[e] for eight values, as predicated selects (no branch).
+__device__ __forceinline__ void select8(float* r, const float* v, uint32_t take) {
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %8, 0;\n\t"
+        "selp.f32 %0, %9, %0, q;\n\tselp.f32 %1, %10, %1, q;\n\t"
+        "selp.f32 %2, %11, %2, q;\n\tselp.f32 %3, %12, %3, q;\n\t"
+        "selp.f32 %4, %13, %4, q;\n\tselp.f32 %5, %14, %5, q;\n\t"
+        "selp.f32 %6, %15, %6, q;\n\tselp.f32 %7, %16, %7, q;\n\t}"
+        : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]), "+f"(r[6]), "+f"(r[7])
+        : "r"(take), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
+}
 
 __device__ __forceinline__ bool aborted(const Ctl& c) {
     return *reinterpret_cast<const volatile int*>(&c.abort) != 0;
@@ -94,6 +114,7 @@ struct Params {
     int stages, nob;                // operand stages; store buffers per epilogue warp
     const float* anrm;              // SIM: |a_i|^2 (length >= M)
     const float* bnrm;              // |b_k|^2 (length >= N rounded up to BN)
+    int snrm;                       // ARGMAX/TOP2: entries of bnrm staged in shared memory (0: read global)
     int32_t* arg;                   // ARGMAX/TOP2: best column per row
     float* best;                    // ARGMAX/TOP2: best score per row (may be null)
     int32_t* arg2;                  // TOP2: second-best column per row (-1: none)
@@ -391,9 +412,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t uj = 0;                             // units this warp has finished
         bool dead = false;
         const uint32_t lane_off = (uint32_t)(sub * 32) << 16;
+        // ARGMAX/TOP2: the column norms, staged once in shared memory when they
+        // fit (the epilogue warps copy them and meet on named barrier 1)
+        float* snrm = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(&sl) + sizeof(Slots));
+        if (amax && p.snrm > 0) {
+            for (int k = threadIdx.x - 64; k < p.snrm / 4; k += 32 * EPI_WARPS)
+                reinterpret_cast<float4*>(snrm)[k] = __ldg(reinterpret_cast<const float4*>(p.bnrm) + k);
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
+        }
+        const float* nrm = (amax && p.snrm > 0) ? snrm : p.bnrm;
         for (int u = blockIdx.x; u < units && !dead; u += gridDim.x) {
             float best = -INFINITY;                  // ARGMAX/TOP2: max of x.e - |e|^2/2
             int bidx = INT_MAX;
+            int bchunk = -1;                         // ARGMAX: first column of the chunk holding best
+            float keep[32];                          // ARGMAX: that chunk's scores
+#pragma unroll
+            for (int e = 0; e < 32; ++e) keep[e] = 0.f;
             float best2 = -INFINITY;                 // TOP2: the runner-up
             int bidx2 = INT_MAX;
             int m0 = 0;
@@ -500,22 +534,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                 } else {
                     // running arg-max of x.e - |e|^2 / 2 (half the score: exact scaling)
                     const float2 mhalf = make_float2(-0.5f, -0.5f);
-                    const float* bn = p.bnrm + col_half;
                     const bool full_tile = col_half + 128 <= p.N;
                     uint32_t ra[32], rb[32];
-                    // ARGMAX: each 32-column chunk's maximum by a max tree, then, only
-                    // where it beats the running best, the chunk's first column
-                    // attaining it (lowest column on ties; chunks arrive in
-                    // increasing column order, so a strict compare keeps the
-                    // earlier chunk).  TOP2 also keeps the runner-up (the best of the
+                    // ARGMAX: each 32-column chunk's maximum by a tree of three-input
+                    // maxima; where it beats the running best (strictly: chunks
+                    // arrive in increasing column order, so a tie keeps the earlier
+                    // chunk) the chunk's scores replace the kept ones by predicated
+                    // selects.  The column inside the kept chunk is found once per
+                    // row block.  TOP2 also keeps the runner-up (the best of the
                     // other columns, lowest column on ties), column by column.
                     auto scan = [&](uint32_t (&v)[32], int c, auto top2) {
                         const int kcol = col_half + c * OUT_COLS;
                         const bool ragged = !full_tile && kcol + OUT_COLS > p.N;
+                        const float4* bn4 = reinterpret_cast<const float4*>(nrm + kcol);
                         float sc[32];
 #pragma unroll
                         for (int u4 = 0; u4 < 8; ++u4) {
-                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bn + c * OUT_COLS) + u4);
+                            const float4 b4 = bn4[u4];
                             const float2 lo = __ffma2_rn(mhalf, make_float2(b4.x, b4.y),
                                                          make_float2(__uint_as_float(v[4 * u4]),
                                                                      __uint_as_float(v[4 * u4 + 1])));
@@ -543,20 +578,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 best = fmaxf(best, sc[e]);
                             }
                         } else {
-                            float t[16];
+                            float t[11];
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) t[e] = fmaxf(sc[2 * e], sc[2 * e + 1]);
+                            for (int e = 0; e < 10; ++e) t[e] = max3f(sc[3 * e], sc[3 * e + 1], sc[3 * e + 2]);
+                            t[10] = fmaxf(sc[30], sc[31]);
+                            const float m = fmaxf(max3f(max3f(t[0], t[1], t[2]), max3f(t[3], t[4], t[5]),
+                                                        max3f(t[6], t[7], t[8])),
+                                                  fmaxf(t[9], t[10]));
+                            const uint32_t imp = m > best ? 1u : 0u;
 #pragma unroll
-                            for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                                for (int e = 0; e < w; ++e) t[e] = fmaxf(t[e], t[e + w]);
-                            if (t[0] > best) {
-                                int j = 31;
-#pragma unroll
-                                for (int e = 30; e >= 0; --e) j = (sc[e] == t[0]) ? e : j;
-                                best = t[0];
-                                bidx = kcol + j;
-                            }
+                            for (int h = 0; h < 4; ++h) select8(keep + 8 * h, sc + 8 * h, imp);
+                            best = imp ? m : best;
+                            bchunk = imp ? kcol : bchunk;
                         }
                         __syncwarp();                    // converged for the next tcgen05 op
                     };
@@ -583,6 +616,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                 acc ^= 1;
             }
             if (dead) break;
+            if (p.mode == ARGMAX && bchunk >= 0) {
+                // the first column of the kept chunk attaining the row's best
+                int j = 31;
+#pragma unroll
+                for (int e = 30; e >= 0; --e) j = (keep[e] == best) ? e : j;
+                bidx = bchunk + j;
+            }
             if (amax) {
                 // merge the two column halves of each row: the larger score,
                 // the lower column on a tie (TOP2: the runner-up of the union
@@ -705,8 +745,19 @@ static int32_t launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensor
     int sms = 0;
     AP_TRY(device_sm_count(&sms));
     layout_for(p.mode, p.K / BK, &p.stages, &p.nob);
-    const size_t bytes = smem_bytes(p.mode, p.stages, p.nob);
+    size_t bytes = smem_bytes(p.mode, p.stages, p.nob);
     if (bytes > (size_t)SMEM_LIMIT) return AP_ERR_UNSUPPORTED;
+    // ARGMAX/TOP2: the column norms go to shared memory when they fit beside
+    // the operand ring (up to about 7900 columns); otherwise they are read
+    // from global memory
+    p.snrm = 0;
+    if (p.mode != SIM) {
+        const size_t npad = (size_t)(p.N + BN - 1) / BN * BN;
+        if (bytes + npad * 4 <= (size_t)SMEM_LIMIT) {
+            p.snrm = (int)npad;
+            bytes += npad * 4;
+        }
+    }
     AP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      SMEM_LIMIT));
     // persistent: one CTA per SM, each taking every gridDim-th unit

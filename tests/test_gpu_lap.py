@@ -108,6 +108,20 @@ def test_lap_assign_full_shape(c_case, n, c, seed):
     assert frac_fp64 <= 0.02
 
 
+def test_lap_assign_with_more_centres_than_the_shared_norm_table():
+    """8000 centres: their norms (8192 padded entries) do not fit in shared
+    memory beside the operand ring, so the arg-max epilogue reads them from
+    global memory; 32 column tiles merged by the running arg-max."""
+    n, c = 10000, 8000
+    X = _data(n=n, d=16, k=40, seed=8)
+    E = np.random.default_rng(8).choice(n, c, replace=False).astype(np.int64)
+    idx, best = capi.lap_assign(torch.from_numpy(X).cuda(), torch.from_numpy(E), best=True)
+    labels = idx.cpu().numpy().astype(np.int64)
+    frac_clear, frac_fp64 = _check_assignment(X, E, labels, best.cpu().numpy().astype(np.float64))
+    print(f"\nlap_assign n={n} c={c}: clear {frac_clear:.4f}, differ from float64 {frac_fp64:.2e}")
+    assert frac_clear > 0.8
+
+
 def test_lap_run_full_shape_assignment():
     """lap_run (Steps 1-2) on 20000 points of the 1e6-point 128-D workload
     generator with 3000 uniform landmarks: several hundred exemplars (three or
