@@ -308,7 +308,12 @@ int32_t   lap_run(const float* X, int64_t n, int64_t d, int64_t ldx, int64_t n_l
  *           computed as argmax_j (2 x_i.e_j - |e_j|^2) by the bf16 tensor-core
  *           GEMM of the mean-centred features with fp32 accumulation (the
  *           arg-max fused into its epilogue, the n x c scores never written);
- *           centres keep themselves.
+ *           centres keep themselves.  Up to 1024 centres the -|e_j|^2 term
+ *           enters the product as an extra bf16 MMA (an exact three-term
+ *           split), beyond that the epilogue subtracts it: the two agree
+ *           within the fp32 accumulation bound.  The environment variable
+ *           APGB_ASSIGN_NORMS = folded | shared | global forces a form where
+ *           it fits (for comparing them; every LAP entry point obeys it).
  *  best     device float [n] out or NULL: that maximum score, on the centred
  *           bf16-rounded features (|x_i|^2 - best is the squared distance).
  *  ws       lap_assign_workspace_size(n, d, c) bytes.  Synchronous.

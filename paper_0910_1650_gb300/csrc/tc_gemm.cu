@@ -6,7 +6,10 @@
 //                  (one persistent launch over a whole batch);
 //   * assignment:  c_i = argmax_j (2 x_i . e_j - |e_j|^2) over the exemplars
 //                  e_j (Algorithm 3 Step 2: nearest centre), never writing the
-//                  N x c score matrix.
+//                  N x c score matrix.  Up to 1024 exemplars, -|e_j|^2/2 enters
+//                  the product through one extra K = 16 MMA per tile over
+//                  augmented operands resident in shared memory; beyond, the
+//                  epilogue subtracts it.
 // Operands are bf16, K-major, loaded by TMA with 128-byte swizzle; the
 // product accumulates in fp32 in tensor memory.
 //
@@ -36,6 +39,8 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -115,6 +120,8 @@ struct Params {
     const float* anrm;              // SIM: |a_i|^2 (length >= M)
     const float* bnrm;              // |b_k|^2 (length >= N rounded up to BN)
     int snrm;                       // ARGMAX/TOP2: entries of bnrm staged in shared memory (0: read global)
+    int aug;                        // ARGMAX/TOP2: groups of 1024 columns whose -|b|^2/2 the MMA adds
+                                    // through the resident augmented operands (0: the epilogue does)
     int32_t* arg;                   // ARGMAX/TOP2: best column per row
     float* best;                    // ARGMAX/TOP2: best score per row (may be null)
     int32_t* arg2;                  // TOP2: second-best column per row (-1: none)
@@ -240,6 +247,47 @@ __device__ __forceinline__ uint64_t smem_desc(const void* base) {
     return d;
 }
 
+// The augmented operands that fold -|b|^2/2 into the product, in the layout
+// of the operand tiles (K-major, 128-byte rows, 128-byte swizzle: 16-byte
+// unit c of row r sits at unit c ^ (r % 8)).  K block k (16 columns: units
+// 2k and 2k+1) of
+//   A' (BM rows):          1, 1, 1, 0, ..., 0 in every row and every block;
+//   B' group g (BN rows):  row r of block k belongs to column g*1024 + k*256 + r
+//                          and holds -h, -m, -l, 0, ..., 0, where h + m + l =
+//                          |b|^2/2 exactly (three bf16 terms of a normal
+//                          float); zero past `ncols`.
+// One K = 16 MMA over block q % 4 of A' and of B' group q / 4 adds -|b|^2/2
+// to every row of column tile q.
+__device__ void build_augmented(uint8_t* aug, const float* bnrm, int ncols, int groups) {
+    auto pack = [](__nv_bfloat16 lo, __nv_bfloat16 hi) -> uint32_t {
+        return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    };
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+    for (int i = threadIdx.x; i < BM * 8; i += blockDim.x) {
+        const int r = i >> 3, c = i & 7;
+        const uint4 v = (c & 1) ? make_uint4(0, 0, 0, 0) : make_uint4(pack(one, one), pack(one, zero), 0, 0);
+        *reinterpret_cast<uint4*>(aug + r * 128 + ((c ^ (r & 7)) << 4)) = v;
+    }
+    uint8_t* bb = aug + A_BYTES;
+    for (int i = threadIdx.x; i < groups * BN * 4; i += blockDim.x) {
+        const int k = i & 3, r = (i >> 2) % BN, g = (i >> 2) / BN;
+        const int col = g * 4 * BN + k * BN + r;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (col < ncols) {
+            const float x = 0.5f * __ldg(bnrm + col);
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(h);                // exact
+            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));   // exact
+            v.x = pack(__hneg(h), __hneg(m));
+            v.y = pack(__hneg(l), zero);
+        }
+        uint8_t* row = bb + (size_t)g * B_BYTES + r * 128;
+        *reinterpret_cast<uint4*>(row + (((2 * k) ^ (r & 7)) << 4)) = v;
+        *reinterpret_cast<uint4*>(row + (((2 * k + 1) ^ (r & 7)) << 4)) = make_uint4(0, 0, 0, 0);
+    }
+}
+
 // Instruction descriptor: kind::f16 with bf16 A/B, fp32 D, both K-major.
 __host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
     return (1u << 4)                  // D format: f32
@@ -289,7 +337,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~uintptr_t(1023));
     uint8_t* out_base = base + (size_t)p.stages * STAGE_BYTES;
-    Ctl& sm = *reinterpret_cast<Ctl*>(out_base + (size_t)EPI_WARPS * p.nob * WBUF_BYTES);
+    // ARGMAX/TOP2 with folded norms: the augmented operands (A' then the B'
+    // groups, 1024-byte aligned) sit between the store buffers and Ctl
+    uint8_t* aug_base = out_base + (size_t)EPI_WARPS * p.nob * WBUF_BYTES;
+    Ctl& sm = *reinterpret_cast<Ctl*>(aug_base + (p.aug > 0 ? (size_t)A_BYTES + (size_t)p.aug * B_BYTES : 0));
     Slots& sl = *reinterpret_cast<Slots*>(reinterpret_cast<uint8_t*>(&sm) + sizeof(Ctl));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -320,6 +371,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         sm.abort = 0;
     }
     if (warp == 1) tmem_alloc(&sm.tmem_base, TMEM_COLS);
+    if (p.aug > 0) {
+        build_augmented(aug_base, p.bnrm, numN * BN, p.aug);
+        ptx::fence_proxy_async_smem();               // generic stores -> the MMA's reads
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -388,6 +443,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                         mma_commit(&sm.empty[stage]);  // frees the stage once these MMAs are done
                         stage = (stage + 1 == ns) ? 0 : stage + 1;
+                    }
+                    if (p.aug > 0) {
+                        // + 1 . (-h - m - l) = -|b|^2/2 for every row: column tile q is
+                        // K block q % 4 of B' group q / 4 (A' holds the ones in every block)
+                        const uint64_t ad = smem_desc(aug_base) + (uint64_t)((q & 3) * 2);
+                        const uint64_t bd = smem_desc(aug_base + A_BYTES + (size_t)(q >> 2) * B_BYTES) +
+                                            (uint64_t)((q & 3) * 2);
+                        mma_bf16(d, ad, bd, idesc, 1u);
                     }
                     mma_commit(&sm.tfull[acc]);        // accumulator ready for the epilogue
                     acc ^= 1;
@@ -543,24 +606,30 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // selects.  The column inside the kept chunk is found once per
                     // row block.  TOP2 also keeps the runner-up (the best of the
                     // other columns, lowest column on ties), column by column.
-                    auto scan = [&](uint32_t (&v)[32], int c, auto top2) {
+                    // fold: the MMA has added -|e|^2/2 already (augmented operands)
+                    auto scan = [&](uint32_t (&v)[32], int c, auto top2, auto fold) {
                         const int kcol = col_half + c * OUT_COLS;
                         const bool ragged = !full_tile && kcol + OUT_COLS > p.N;
                         const float4* bn4 = reinterpret_cast<const float4*>(nrm + kcol);
                         float sc[32];
+                        if (decltype(fold)::value) {
 #pragma unroll
-                        for (int u4 = 0; u4 < 8; ++u4) {
-                            const float4 b4 = bn4[u4];
-                            const float2 lo = __ffma2_rn(mhalf, make_float2(b4.x, b4.y),
-                                                         make_float2(__uint_as_float(v[4 * u4]),
-                                                                     __uint_as_float(v[4 * u4 + 1])));
-                            const float2 hi = __ffma2_rn(mhalf, make_float2(b4.z, b4.w),
-                                                         make_float2(__uint_as_float(v[4 * u4 + 2]),
-                                                                     __uint_as_float(v[4 * u4 + 3])));
-                            sc[4 * u4] = lo.x;
-                            sc[4 * u4 + 1] = lo.y;
-                            sc[4 * u4 + 2] = hi.x;
-                            sc[4 * u4 + 3] = hi.y;
+                            for (int e = 0; e < 32; ++e) sc[e] = __uint_as_float(v[e]);
+                        } else {
+#pragma unroll
+                            for (int u4 = 0; u4 < 8; ++u4) {
+                                const float4 b4 = bn4[u4];
+                                const float2 lo = __ffma2_rn(mhalf, make_float2(b4.x, b4.y),
+                                                             make_float2(__uint_as_float(v[4 * u4]),
+                                                                         __uint_as_float(v[4 * u4 + 1])));
+                                const float2 hi = __ffma2_rn(mhalf, make_float2(b4.z, b4.w),
+                                                             make_float2(__uint_as_float(v[4 * u4 + 2]),
+                                                                         __uint_as_float(v[4 * u4 + 3])));
+                                sc[4 * u4] = lo.x;
+                                sc[4 * u4 + 1] = lo.y;
+                                sc[4 * u4 + 2] = hi.x;
+                                sc[4 * u4 + 3] = hi.y;
+                            }
                         }
                         if (ragged) {
 #pragma unroll
@@ -593,21 +662,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                         __syncwarp();                    // converged for the next tcgen05 op
                     };
-                    auto chunks = [&](auto top2) {
+                    auto chunks = [&](auto top2, auto fold) {
                         tmem_ld32_async(tbase, ra);
                         tmem_wait(ra);
 #pragma unroll
                         for (int c = 0; c < 4; c += 2) {
                             tmem_ld32_async(tbase + (uint32_t)((c + 1) * OUT_COLS), rb);
-                            scan(ra, c, top2);
+                            scan(ra, c, top2, fold);
                             tmem_wait(rb);
                             if (c + 2 < 4) tmem_ld32_async(tbase + (uint32_t)((c + 2) * OUT_COLS), ra);
-                            scan(rb, c + 1, top2);
+                            scan(rb, c + 1, top2, fold);
                             if (c + 2 < 4) tmem_wait(ra);
                         }
                     };
-                    if (p.mode == TOP2) chunks(std::true_type{});
-                    else chunks(std::false_type{});
+                    if (p.mode == TOP2) {
+                        if (p.aug > 0) chunks(std::true_type{}, std::true_type{});
+                        else chunks(std::true_type{}, std::false_type{});
+                    } else {
+                        if (p.aug > 0) chunks(std::false_type{}, std::true_type{});
+                        else chunks(std::false_type{}, std::false_type{});
+                    }
                 }
                 // accumulator drained: hand it back to the MMA warp
                 tc_fence_before();
@@ -729,7 +803,7 @@ static int32_t make_out_map(CUtensorMap* map, float* S, int n, int64_t lds) {
 // Operand stages and store buffers: a long product (K >= 256) wants a deep
 // operand ring and writes S slowly; a short one is bound by writing S.
 static void layout_for(int mode, int numK, int* stages, int* nob) {
-    if (mode != SIM) { *stages = 4; *nob = 0; }
+    if (mode != SIM) { *stages = 3; *nob = 0; }   // (measured no slower than 4 at K = 128)
     else if (numK >= 4) { *stages = 4; *nob = 1; }
     else if (numK >= 2) { *stages = 3; *nob = 2; }
     else { *stages = 2; *nob = 4; }
@@ -740,6 +814,19 @@ static size_t smem_bytes(int mode, int stages, int nob) {
            (mode != SIM ? sizeof(Slots) : 0);
 }
 
+// ARGMAX/TOP2 norm form: 0 automatic (the first that fits of folded, shared
+// table, global); the environment variable APGB_ASSIGN_NORMS = folded |
+// shared | global asks for one form (taken where it fits, else the next), so
+// the three can be compared on the same inputs.
+static int assign_norm_form() {
+    const char* e = std::getenv("APGB_ASSIGN_NORMS");
+    if (!e) return 0;
+    if (!std::strcmp(e, "folded")) return 1;
+    if (!std::strcmp(e, "shared")) return 2;
+    if (!std::strcmp(e, "global")) return 3;
+    return 0;
+}
+
 static int32_t launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& o, Params p,
                       int units, cudaStream_t s) {
     int sms = 0;
@@ -747,13 +834,22 @@ static int32_t launch(const CUtensorMap& a, const CUtensorMap& b, const CUtensor
     layout_for(p.mode, p.K / BK, &p.stages, &p.nob);
     size_t bytes = smem_bytes(p.mode, p.stages, p.nob);
     if (bytes > (size_t)SMEM_LIMIT) return AP_ERR_UNSUPPORTED;
-    // ARGMAX/TOP2: the column norms go to shared memory when they fit beside
-    // the operand ring (up to about 7900 columns); otherwise they are read
-    // from global memory
+    // ARGMAX/TOP2: how -|b|^2/2 enters the scores.  Folded into the product
+    // by one extra K = 16 MMA per tile where the augmented operands fit
+    // (16 KB + 32 KB per 1024 columns: up to 1024 columns); otherwise the
+    // epilogue subtracts it, reading the norms from a shared-memory table
+    // where that fits (up to about 20000 columns) or from global memory.
     p.snrm = 0;
+    p.aug = 0;
     if (p.mode != SIM) {
         const size_t npad = (size_t)(p.N + BN - 1) / BN * BN;
-        if (bytes + npad * 4 <= (size_t)SMEM_LIMIT) {
+        const int groups = (int)((npad + 4 * BN - 1) / (4 * BN));
+        const size_t augb = (size_t)A_BYTES + (size_t)groups * B_BYTES;
+        const int want = assign_norm_form();
+        if (want <= 1 && bytes + augb <= (size_t)SMEM_LIMIT) {
+            p.aug = groups;
+            bytes += augb;
+        } else if (want <= 2 && bytes + npad * 4 <= (size_t)SMEM_LIMIT) {
             p.snrm = (int)npad;
             bytes += npad * 4;
         }

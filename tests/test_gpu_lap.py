@@ -108,6 +108,28 @@ def test_lap_assign_full_shape(c_case, n, c, seed):
     assert frac_fp64 <= 0.02
 
 
+@pytest.mark.parametrize("c", [700, 1024])
+def test_lap_assign_norm_forms(c, monkeypatch):
+    """The three ways -|e|^2/2 enters the arg-max GEMM's scores, on the same
+    inputs: folded into the product by an extra MMA over the augmented
+    operands (the default up to 1024 centres), subtracted in the epilogue
+    from a shared-memory table, or from global memory.  Each is checked
+    against the oracle; the two epilogue forms agree bit for bit."""
+    n = 6000
+    X, _ = synth.workload(3, scale=n / 1_000_000)
+    X = np.ascontiguousarray(X[:n])
+    E = np.random.default_rng(c).choice(n, c, replace=False).astype(np.int64)
+    got = {}
+    for form in ("folded", "shared", "global"):
+        monkeypatch.setenv("APGB_ASSIGN_NORMS", form)
+        idx, best = capi.lap_assign(torch.from_numpy(X).cuda(), torch.from_numpy(E), best=True)
+        got[form] = (idx.cpu().numpy().astype(np.int64), best.cpu().numpy().astype(np.float64))
+        frac_clear, _ = _check_assignment(X, E, got[form][0], got[form][1])
+        assert frac_clear > 0.8, form
+    assert np.array_equal(got["shared"][0], got["global"][0])
+    assert np.array_equal(got["shared"][1], got["global"][1])
+
+
 def test_lap_assign_with_more_centres_than_the_shared_norm_table():
     """8000 centres: their norms (8192 padded entries) do not fit in shared
     memory beside the operand ring, so the arg-max epilogue reads them from
