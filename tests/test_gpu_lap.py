@@ -283,12 +283,16 @@ def _integer_clusters(seed, k=20, per=30, d=16, spread=3):
     return np.vstack([P, -P]).astype(np.float32)
 
 
-@pytest.mark.parametrize("seed", [3, 4, 6])
-def test_lap_refine_matches_oracle_exactly_on_integer_data(seed):
+@pytest.mark.parametrize("seed,form", [(3, None), (4, None), (6, None), (3, "shared"), (4, "global")])
+def test_lap_refine_matches_oracle_exactly_on_integer_data(seed, form, monkeypatch):
     """The refinement against the oracle's, decision for decision: seeds whose
     medoid choices are all clear (two members at the same distance from the
     class mean in exact arithmetic may round apart differently under the two
-    summation orders; the precondition is asserted)."""
+    summation orders; the precondition is asserted).  On integer data every
+    norm form of the top-2 GEMM (folded by default at this size, or the
+    epilogue's shared or global norms) is exact."""
+    if form:
+        monkeypatch.setenv("APGB_ASSIGN_NORMS", form)
     X = _integer_clusters(seed, spread=5)
     n = X.shape[0]
     g = np.random.default_rng(50 + seed)
