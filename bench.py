@@ -982,6 +982,28 @@ def lap_only(args):
           flush=True)
 
 
+def lap_full_only(args):
+    """Algorithm 3 in full (Steps 1-4, the refinement included) on all 1e6
+    points of the 1e6-point workload, once, as the time-to-converge section
+    runs it; for the launch list of that call."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi, synth
+
+    X, _ = synth.workload(3)
+    Xd = torch.from_numpy(X).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    _, _, r = capi.lap_run_full(Xd, 20000, 20000, seed=synth.config_seed(3), precision="bf16",
+                                damping=DAMPING, max_iter=MAX_ITER, conv_iter=CONV_ITER,
+                                refine_rounds=REFINE_ROUNDS)
+    ev[1].record()
+    ev[1].synchronize()
+    print(json.dumps({"case": "lap_full", "n": X.shape[0], "ms": round(ev[0].elapsed_time(ev[1]), 1),
+                      "levels": r["levels"], "unassigned": r["unassigned"][:r["levels"]],
+                      "n_exemplars": r["n_exemplars"], "refine_rounds": r["refine_rounds"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1004,6 +1026,9 @@ def main():
     ap.add_argument("--lap-only", type=int, default=0, metavar="N",
                     help="profiling aid: one landmark AP (Steps 1-2, 20000 landmarks, bf16) on the "
                          "first N points of the 1e6-point workload, print one JSON line")
+    ap.add_argument("--lap-full-only", action="store_true",
+                    help="profiling aid: one call of Algorithm 3 Steps 1-4 (refined) on all 1e6 "
+                         "points, print one JSON line")
     ap.add_argument("--similarity-only", type=int, default=0, metavar="D",
                     help="profiling aid: time the bf16 similarity build alone on one image-like "
                          "problem of --n points and D features, print one JSON line")
@@ -1019,6 +1044,9 @@ def main():
         return
     if args.lap_only:
         lap_only(args)
+        return
+    if args.lap_full_only:
+        lap_full_only(args)
         return
     if args.pap_table2:
         import torch

@@ -98,51 +98,145 @@ __global__ void kselect_scan_kernel(KSelect* st, unsigned* hist) {
     for (int x = 0; x < 256; ++x) hist[x] = 0;
 }
 
-// Single block, index order: keys below the threshold, then as many keys
-// equal to it as are needed (lowest indices first).  out is ascending.
-__global__ void kselect_compact_kernel(const uint64_t* __restrict__ keys, int64_t n,
-                                       const KSelect* __restrict__ st, int64_t L, int32_t* out) {
-    __shared__ int wsum[32], weq[32];
-    __shared__ int64_t base;
-    __shared__ int64_t ties_left;
-    const uint64_t thr = st->prefix;
-    if (threadIdx.x == 0) {
-        base = 0;
-        ties_left = L - (int64_t)st->less;
-    }
-    __syncthreads();
+// ---- order-preserving compaction over up to kCompactBlocks blocks -------------
+// Block b owns the contiguous range [b * chunk, min(n, (b + 1) * chunk)).  A
+// count kernel stores each block's counts; the write kernel adds the counts of
+// the blocks before its own (at most kCompactBlocks) and places every selected
+// index at its rank among the selected ones, so the output is ascending.
+constexpr int kCompactBlocks = 256;
+
+static int compact_blocks(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kCompactBlocks, (n + 1023) / 1024));
+}
+
+// Sum of a block's thread values (blockDim.x a multiple of 32, at most 1024).
+__device__ __forceinline__ int block_sum(int v, int* red) {
     const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t lo = 0; lo < n; lo += blockDim.x) {
-        const int64_t i = lo + threadIdx.x;
-        const uint64_t k = (i < n) ? keys[i] : ~0ull;
-        const bool lt = i < n && k < thr;
-        const bool eq = i < n && k == thr;
-        const unsigned blt = __ballot_sync(0xffffffffu, lt), beq = __ballot_sync(0xffffffffu, eq);
-        if (lid == 0) { wsum[wid] = __popc(blt); weq[wid] = __popc(beq); }
-        __syncthreads();
-        int before_lt = 0, before_eq = 0;
-        for (int w = 0; w < wid; ++w) { before_lt += wsum[w]; before_eq += weq[w]; }
-        const int my_eq = before_eq + __popc(beq & ((1u << lid) - 1u));
-        const bool take_eq = eq && my_eq < ties_left;
-        // slots before this thread: all lt and taken eq of lower indices
-        int taken_eq_before = 0;
-        for (int w = 0; w < wid; ++w) taken_eq_before += weq[w];
-        {
-            const int64_t cand = (int64_t)taken_eq_before + __popc(beq & ((1u << lid) - 1u));
-            taken_eq_before = (int)(cand < ties_left ? cand : ties_left);
-        }
-        const int64_t pos = base + before_lt + __popc(blt & ((1u << lid) - 1u)) + taken_eq_before;
-        if (lt || take_eq) out[pos] = (int32_t)i;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tl = 0, te = 0;
-            for (int w = 0; w < nw; ++w) { tl += wsum[w]; te += weq[w]; }
-            const int64_t te_taken = te < ties_left ? (int64_t)te : ties_left;
-            base += tl + te_taken;
-            ties_left -= te_taken;
-        }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lid == 0) red[wid] = v;
+    __syncthreads();
+    int t = 0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+// Sum of cnt[0 .. b-1] (b <= kCompactBlocks), in every thread.
+__device__ __forceinline__ int64_t counts_before(const unsigned* __restrict__ cnt, int b, int* red) {
+    int v = 0;
+    for (int c = threadIdx.x; c < b; c += blockDim.x) v += (int)cnt[c];
+    return block_sum(v, red);
+}
+
+// Landmark selection: per block, the keys below the threshold (cnt[b]) and
+// equal to it (cnt[kCompactBlocks + b]).
+__global__ void kselect_count_kernel(const uint64_t* __restrict__ keys, int64_t n, int64_t chunk,
+                                     const KSelect* __restrict__ st, unsigned* cnt) {
+    __shared__ int red[32];
+    const uint64_t thr = st->prefix;
+    const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    int lt = 0, eq = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint64_t k = keys[i];
+        lt += k < thr;
+        eq += k == thr;
     }
+    lt = block_sum(lt, red);
+    eq = block_sum(eq, red);
+    if (threadIdx.x == 0) {
+        cnt[blockIdx.x] = (unsigned)lt;
+        cnt[kCompactBlocks + blockIdx.x] = (unsigned)eq;
+    }
+}
+
+// Index order: every key below the threshold, then as many keys equal to it
+// as are needed (the lowest indices).  out is ascending.
+__global__ void kselect_write_kernel(const uint64_t* __restrict__ keys, int64_t n, int64_t chunk,
+                                     const KSelect* __restrict__ st, int64_t L,
+                                     const unsigned* __restrict__ cnt, int32_t* out) {
+    __shared__ int red[32], wlt[32], weq[32];
+    const uint64_t thr = st->prefix;
+    const int64_t ties = L - (int64_t)st->less;             // keys equal to thr to take
+    int64_t lt_base = counts_before(cnt, blockIdx.x, red);
+    int64_t eq_base = counts_before(cnt + kCompactBlocks, blockIdx.x, red);
+    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int64_t b0 = lo; b0 < hi; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        const uint64_t k = (i < hi) ? keys[i] : ~0ull;
+        const bool lt = i < hi && k < thr, eq = i < hi && k == thr;
+        const unsigned blt = __ballot_sync(0xffffffffu, lt), beq = __ballot_sync(0xffffffffu, eq);
+        __syncthreads();                                    // the previous step read wlt, weq
+        if (lid == 0) { wlt[wid] = __popc(blt); weq[wid] = __popc(beq); }
+        __syncthreads();
+        int64_t lt_before = lt_base, eq_before = eq_base;
+        int tl = 0, te = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) { lt_before += wlt[w]; eq_before += weq[w]; }
+            tl += wlt[w];
+            te += weq[w];
+        }
+        const unsigned below = (1u << lid) - 1u;
+        lt_before += __popc(blt & below);
+        eq_before += __popc(beq & below);
+        if (lt || (eq && eq_before < ties))
+            out[lt_before + (eq_before < ties ? eq_before : ties)] = (int32_t)i;
+        lt_base += tl;
+        eq_base += te;
+    }
+}
+
+// out = the indices i < n with flags[i] != 0, ascending; *count their number.
+// Per block, the flags set (cnt[b]).
+__global__ void flags_count_kernel(const int32_t* __restrict__ flags, int64_t n, int64_t chunk,
+                                   unsigned* cnt) {
+    __shared__ int red[32];
+    const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    int f = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) f += flags[i] != 0;
+    f = block_sum(f, red);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (unsigned)f;
+}
+
+__global__ void flags_write_kernel(const int32_t* __restrict__ flags, int64_t n, int64_t chunk,
+                                   const unsigned* __restrict__ cnt, int32_t* out, int32_t* count) {
+    __shared__ int red[32], wsum[32];
+    int64_t base = counts_before(cnt, blockIdx.x, red);
+    if (blockIdx.x == gridDim.x - 1) {
+        const int64_t own = (threadIdx.x == 0) ? (int64_t)cnt[blockIdx.x] : 0;
+        if (threadIdx.x == 0) *count = (int32_t)(base + own);
+    }
+    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int64_t b0 = lo; b0 < hi; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        const bool f = i < hi && flags[i] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        __syncthreads();                                    // the previous step read wsum
+        if (lid == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int64_t before = base;
+        int t = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) before += wsum[w];
+            t += wsum[w];
+        }
+        if (f) out[before + __popc(bal & ((1u << lid) - 1u))] = (int32_t)i;
+        base += t;
+    }
+}
+
+// The order-preserving compaction of the flags set; cnt: kCompactBlocks
+// entries of scratch.
+static int32_t compact_flags(const int32_t* flags, int64_t n, int32_t* out, int32_t* count,
+                             unsigned* cnt, cudaStream_t s) {
+    const int nb = compact_blocks(n);
+    const int64_t chunk = (n + nb - 1) / nb;
+    flags_count_kernel<<<nb, 1024, 0, s>>>(flags, n, chunk, cnt);
+    flags_write_kernel<<<nb, 1024, 0, s>>>(flags, n, chunk, cnt, out, count);
+    note_launches(2);
+    return last_error();
 }
 
 // ---- gathers, centring, labels, netsim -------------------------------------------
@@ -318,34 +412,6 @@ __global__ void gate_kernel(int64_t nl, const int32_t* __restrict__ arg,
         un[i] = ok ? 0 : 1;
         if (ok && level_of) level_of[ids ? ids[i] : i] = level;
     }
-}
-
-// out = the indices i < n with flags[i] != 0, ascending; *count their number.
-__global__ void compact_flags_kernel(const int32_t* __restrict__ flags, int64_t n, int32_t* out,
-                                     int32_t* count) {
-    __shared__ int wsum[32];
-    __shared__ int64_t base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lid = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t lo = 0; lo < n; lo += blockDim.x) {
-        const int64_t i = lo + threadIdx.x;
-        const bool f = i < n && flags[i] != 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lid == 0) wsum[wid] = __popc(bal);
-        __syncthreads();
-        int before = 0;
-        for (int w = 0; w < wid; ++w) before += wsum[w];
-        if (f) out[base + before + __popc(bal & ((1u << lid) - 1u))] = (int32_t)i;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < nw; ++w) t += wsum[w];
-            base += t;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *count = (int32_t)base;
 }
 
 // out[j] = ids[local[j]] (ids == NULL: the identity); level_of of those set.
@@ -537,7 +603,7 @@ static size_t carve_lap(void* ws, int64_t n, int64_t d, int64_t L, LapWs* w) {
     Carver c(ws);
     w->keys = c.take<uint64_t>(n);
     w->ks = c.take<KSelect>(1);
-    w->hist = c.take<unsigned>(256);
+    w->hist = c.take<unsigned>(256 + 2 * kCompactBlocks);   // radix bins, then compaction counts
     w->lm = c.take<int32_t>(L);
     w->XL = c.take<float>((size_t)L * d);
     w->SL = c.take<float>((size_t)L * ldL);
@@ -568,8 +634,11 @@ static int32_t select_smallest(const uint64_t* keys, int64_t n, int64_t L, KSele
         kselect_hist_kernel<<<grid, 256, 0, s>>>(keys, n, ks, hist);
         kselect_scan_kernel<<<1, 32, 0, s>>>(ks, hist);
     }
-    kselect_compact_kernel<<<1, 1024, 0, s>>>(keys, n, ks, L, out);
-    note_launches(18);
+    const int nb = compact_blocks(n);
+    const int64_t chunk = (n + nb - 1) / nb;
+    kselect_count_kernel<<<nb, 1024, 0, s>>>(keys, n, chunk, ks, hist + 256);
+    kselect_write_kernel<<<nb, 1024, 0, s>>>(keys, n, chunk, ks, L, hist + 256, out);
+    note_launches(19);
     return last_error();
 }
 
@@ -1112,9 +1181,9 @@ APGB_API int32_t lap_run_full(const float* X, int64_t n, int64_t d, int64_t ldx,
         map_ids_kernel<<<grid_for(c), 256, 0, s>>>(w.lap.epts, c, ids, w.E + nE, level, level_of);
         nE += c;
         out->exemplars_at[level] = c;
-        compact_flags_kernel<<<1, 1024, 0, s>>>(w.un, nl, w.list, w.cnt);
-        note_launches(5);
+        note_launches(4);
         AP_TRY(last_error());
+        AP_TRY(compact_flags(w.un, nl, w.list, w.cnt, w.lap.hist + 256, s));
         int32_t m = 0;
         AP_CUDA_TRY(cudaMemcpyAsync(&m, w.cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         AP_CUDA_TRY(cudaStreamSynchronize(s));

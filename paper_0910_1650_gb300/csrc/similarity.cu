@@ -75,17 +75,29 @@ __global__ void __launch_bounds__(256) colsum_partial_kernel(const float* __rest
     colsum_block(X, n, d, ldx, rows, part, blockIdx.x, blockIdx.y);
 }
 
-__device__ __forceinline__ void colmean_at(const double* __restrict__ part, int nb, int d, int64_t n,
-                                           float* mean, int j) {
-    if (j >= d) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * d + j];
-    mean[j] = (float)(s / (double)n);
+// The means from the row blocks' sums: columns bx*32 .. bx*32+31, in the
+// layout of colsum_block (32 columns x 8 lanes; lane y adds blocks y, y+8,
+// ... in order, then the 8 lane sums meet in the same fixed tree), so the
+// float64 chain per thread is nb/8 long (float64 is scarce on this part).
+__device__ __forceinline__ void colmean_block(const double* __restrict__ part, int nb, int d, int64_t n,
+                                              float* mean, int bx) {
+    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+    const int j = bx * 32 + cx;
+    __shared__ double ps[8][32];
+    double sm = 0.0;
+    if (j < d)
+        for (int b = ry; b < nb; b += 8) sm += part[(int64_t)b * d + j];
+    ps[ry][cx] = sm;
+    __syncthreads();
+    if (ry == 0 && j < d)
+        mean[j] = (float)((((ps[0][cx] + ps[1][cx]) + (ps[2][cx] + ps[3][cx])) +
+                           ((ps[4][cx] + ps[5][cx]) + (ps[6][cx] + ps[7][cx]))) / (double)n);
 }
 
-__global__ void colmean_kernel(const double* __restrict__ part, int nb, int d, int64_t n,
-                               float* mean) {
-    colmean_at(part, nb, d, n, mean, blockIdx.x * blockDim.x + threadIdx.x);
+// grid ceil(d/32), 256 threads
+__global__ void __launch_bounds__(256) colmean_kernel(const double* __restrict__ part, int nb, int d,
+                                                      int64_t n, float* mean) {
+    colmean_block(part, nb, d, n, mean, blockIdx.x);
 }
 
 // ---- 2. centring, norms -----------------------------------------------------------
@@ -454,7 +466,7 @@ int32_t column_means(const float* X, int64_t n, int d, int64_t ldx, double* part
                      cudaStream_t s) {
     const int nb = mean_blocks(n);
     colsum_partial_kernel<<<dim3((d + 31) / 32, nb), 256, 0, s>>>(X, n, d, ldx, mean_rows(n), part);
-    colmean_kernel<<<(d + 255) / 256, 256, 0, s>>>(part, nb, d, n, mean);
+    colmean_kernel<<<(d + 31) / 32, 256, 0, s>>>(part, nb, d, n, mean);
     note_launches(2);
     return last_error();
 }
@@ -536,10 +548,10 @@ __global__ void __launch_bounds__(256) colsum_batched_kernel(const SimProblem* _
     colsum_block(q.X, q.n, d, ldx, q.mrows, q.part, blockIdx.y, blockIdx.x - q.part_b0);
 }
 
-// grid (problems, ceil(d/256))
-__global__ void colmean_batched_kernel(const SimProblem* __restrict__ P, int d) {
+// grid (problems, ceil(d/32)), 256 threads
+__global__ void __launch_bounds__(256) colmean_batched_kernel(const SimProblem* __restrict__ P, int d) {
     const SimProblem& q = P[blockIdx.x];
-    colmean_at(q.part, q.nb, d, q.n, q.mean, blockIdx.y * blockDim.x + threadIdx.x);
+    colmean_block(q.part, q.nb, d, q.n, q.mean, blockIdx.y);
 }
 
 // grid (sum of centring blocks)
@@ -820,7 +832,7 @@ APGB_API int32_t ap_similarity_batched(const float* X, const int64_t* xoff, cons
     AP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t) * count, s));
     // 1-2. column means and the centred copies of every problem
     colsum_batched_kernel<<<dim3(part_blocks, (di + 31) / 32), 256, 0, s>>>(table, count, di, ldx);
-    colmean_batched_kernel<<<dim3(count, (di + 255) / 256), 256, 0, s>>>(table, di);
+    colmean_batched_kernel<<<dim3(count, (di + 31) / 32), 256, 0, s>>>(table, di);
     bool vx = (ldx & 3) == 0;
     for (int32_t b = 0; b < count; ++b) vx = vx && aligned16(X + xoff[b]);
     if (bf16) {
