@@ -338,10 +338,11 @@ int32_t   lap_assign(const float* X, int64_t n, int64_t d, int64_t ldx, const in
  *          its own exemplar); else Steps 1-3 on them (the next level, up to
  *          max_levels levels; points still left after the last level join
  *          their nearest exemplar in Step 4).  Exemplars of every level merge.
- *  Step 4  "refine the final set of centers and classes, recalculate the
- *          similarity and obtain the best final results", read as a local
- *          search on net similarity (-E(c), Section 2) over the merged set,
- *          for up to refine_rounds rounds (0: reassignment only).  A round:
+ *  Step 4  (the paper asks for the merged centres and classes to be
+ *          refined, with the similarities recomputed, without a procedure)
+ *          read as a local search on net similarity (-E(c), Section 2) over
+ *          the merged set, for up to refine_rounds rounds (0: reassignment
+ *          only).  A round:
  *            a. every point's nearest and second-nearest centre (the
  *               assignment GEMM with a top-2 epilogue);
  *            b. the cost of dropping centre e, delta(e) = sum over its class

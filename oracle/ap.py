@@ -20,9 +20,9 @@ Two statements of one iteration are given:
 
 Readings of points the paper leaves open:
   * R starts at zero, like A (Eq. 1 names only A).
-  * "each message is set to lambda times its value from the previous
-    iteration plus 1-lambda times its prescribed updated value" (Section 2):
-    R is damped first, A is then computed from the damped R and damped.
+  * Damping (Section 2): a message's new value is lambda times its old one
+    plus 1-lambda times its update; R is damped first, A is then computed
+    from the damped R and damped.
   * Decisions: point i's choice is the lowest k maximising a(i,k)+r(i,k);
     the exemplar set is E = {k : choice(k) == k}.
   * Termination (Step 4): stop once E has been the same, and non-empty, for

@@ -207,9 +207,9 @@ def netsim_rounded(X, E, pref):
 
 
 def refine(X, E, pref, max_rounds=8):
-    """Step 4 ("refine the final set of centers and classes, recalculate the
-    similarity and obtain the best final results"), read as a local search
-    on the net similarity of Section 2 (netsim = -E(c): the summed similarity
+    """Step 4 (the merged centres and their classes are to be refined, with
+    the similarities recomputed; the paper gives no procedure), read as a
+    local search on the net similarity of Section 2 (netsim = -E(c): the summed similarity
     of every point to its centre plus the preference p < 0 of every centre).
     One round:
       1. every point joins its nearest centre j1 (second nearest: j2), on

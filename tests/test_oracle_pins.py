@@ -321,7 +321,7 @@ def test_pap_netsim_close_to_ap():
     ea = ap.exemplars(S, a["R"], a["A"])
     r = pap.run(S, pap.equal_partition(S.shape[0], 4), lam=0.5, max_iter=500)
     er = ap.exemplars(S, r["final"]["R"], r["final"]["A"])
-    # Section 3: the result is "similar to or even better than" plain AP
+    # Section 3: PAP's result matches plain AP's or improves on it
     assert er["netsim"] >= ea["netsim"] * (1 + 0.005)
 
 
