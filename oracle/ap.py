@@ -55,6 +55,23 @@ def similarity(X: np.ndarray, Y: np.ndarray | None = None) -> np.ndarray:
     return S
 
 
+def similarity_gram(X) -> np.ndarray:
+    """Section 2's s(i,k) = -||x_i - x_k||^2 in float64, expanded as
+    2 x_i.x_k - |x_i|^2 - |x_k|^2 (one matrix product), for inputs too large
+    for the explicit differences of ``similarity``.  The diagonal is 0 and
+    every entry is clamped to <= 0, as the definition guarantees; it agrees
+    with ``similarity`` to rounding (pinned)."""
+    X = np.asarray(X, dtype=np.float64)
+    nrm = np.einsum("ij,ij->i", X, X)
+    S = X @ X.T
+    S *= 2.0
+    S -= nrm[:, None]
+    S -= nrm[None, :]
+    np.minimum(S, 0.0, out=S)
+    np.fill_diagonal(S, 0.0)
+    return S
+
+
 def round_bf16(x) -> np.ndarray:
     """float32 -> nearest bfloat16 (ties to even), returned as float32: keep
     the top 16 bits after adding 0x7FFF plus the lowest kept bit."""
@@ -89,6 +106,22 @@ def offdiag_median(S: np.ndarray) -> float:
     if m % 2 == 1:
         return float(vals[m // 2])
     return float(0.5 * (vals[m // 2 - 1] + vals[m // 2]))
+
+
+def offdiag_median_select(S: np.ndarray) -> float:
+    """``offdiag_median`` by selection (np.partition) instead of a full sort:
+    the same order statistics of the N(N-1) off-diagonal entries, for large
+    N (pinned against ``offdiag_median``)."""
+    n = S.shape[0]
+    vals = S[~np.eye(n, dtype=bool)].astype(np.float64)
+    m = vals.size
+    if m == 0:
+        raise ValueError("need at least two points")
+    if m % 2 == 1:
+        return float(np.partition(vals, m // 2)[m // 2])
+    lo = m // 2 - 1
+    part = np.partition(vals, [lo, lo + 1])
+    return float(0.5 * (part[lo] + part[lo + 1]))
 
 
 def tiebreak_noise(n_rows: int, n_cols: int, seed: int) -> np.ndarray:

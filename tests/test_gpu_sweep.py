@@ -113,6 +113,35 @@ def test_every_sweep_configuration_matches_oracle():
     assert {k[0] for k in tried} >= {1, 4, 16}
 
 
+def test_sweep_at_the_bench_size_matches_oracle():
+    """The bench's 20000-point, 64-D mixture in the launch configuration the
+    bench times (the default rule at this size), for two iterations: the
+    first launch (R only), the second (A of iteration 1 fused with R of
+    iteration 2) and the last (A of iteration 2).  Both sides start from the
+    same float32 S, built by the oracle from the points (Section 2's
+    similarity, preference the off-diagonal median); R and A against the
+    float64 oracle within 1e-4 relative."""
+    X, _ = synth.workload(1)
+    S64 = oap.similarity_gram(X)
+    S64 = oap.set_preference(S64, oap.offdiag_median_select(S64))
+    S32 = S64.astype(np.float32)
+    del S64
+    n = S32.shape[0]
+    assert n == 20000
+    S = capi.empty_square(n, "cuda")
+    S.copy_(torch.from_numpy(S32))
+    R, A, res, _ = capi.ap_iterate(S, damping=0.9, max_iter=2, conv_iter=0)
+    assert res["iters"] == 2
+    Rg = R.cpu().numpy()
+    Ag = A.cpu().numpy()
+    del R, A, S
+    ref = oap.run(S32.astype(np.float64), lam=0.9, fixed_iters=2)
+    err = [float(np.abs(got - want).max() / np.abs(want).max())
+           for got, want in ((Rg, ref["R"]), (Ag, ref["A"]))]
+    print(f"\nN=20000, 2 iterations: relative error R {err[0]:.2e}, A {err[1]:.2e}")
+    assert max(err) <= 1e-4
+
+
 @pytest.mark.parametrize("name,lam,maxit,check", [("mix2d_500", 0.5, 200, 0), ("mix2d_500", 0.5, 200, 7),
                                                    ("mix64_2000", 0.9, 300, 0)])
 def test_graph_launch_equals_stream_launch(name, lam, maxit, check):

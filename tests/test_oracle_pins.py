@@ -254,6 +254,32 @@ def test_offdiag_median_by_hand():
     assert ap.offdiag_median(S) == 3.5          # values 1..6: mean of 3 and 4
 
 
+def test_similarity_gram_vs_explicit_differences():
+    """The expanded form used at large N against scipy's squared distances
+    (an independent routine) and the explicit differences: equal to rounding,
+    zero diagonal, never positive (two coincident points give exactly 0)."""
+    g = np.random.default_rng(5)
+    X = (g.normal(size=(300, 64)) * 3 + 10).astype(np.float32)
+    X[17] = X[3]                                     # coincident points
+    Sg = ap.similarity_gram(X)
+    ref = -cdist(X.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+    scale = np.abs(ref).max()
+    assert np.abs(Sg - ref).max() <= 1e-12 * scale
+    assert np.abs(Sg - ap.similarity(X)).max() <= 1e-12 * scale
+    assert (np.diag(Sg) == 0).all() and (Sg <= 0).all()
+    assert Sg[3, 17] == 0.0 and Sg[17, 3] == 0.0
+
+
+@pytest.mark.parametrize("n", [2, 3, 10, 11, 64])
+def test_offdiag_median_select_equals_sorted_median(n):
+    g = np.random.default_rng(100 + n)
+    S = g.normal(size=(n, n))
+    assert ap.offdiag_median_select(S) == ap.offdiag_median(S)
+    T = np.round(S * 2) / 2                          # many ties
+    assert ap.offdiag_median_select(T) == ap.offdiag_median(T)
+    assert ap.offdiag_median_select(T) == float(np.median(T[~np.eye(n, dtype=bool)]))
+
+
 def test_tiebreak_noise_magnitude():
     X, _ = _separated(n_per=5, seed=1)
     S0, p = ap.build_similarity(X)
