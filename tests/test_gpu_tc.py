@@ -54,6 +54,30 @@ def test_bf16_similarity_matches_oracle(name):
     assert (np.diag(S) == np.float32(p)).all()
 
 
+def test_bf16_similarity_at_the_bench_size_sampled_rows():
+    """The bench's 20000-point, 64-D build at full size (the launch the bench
+    times): 66 sampled rows against the oracle's distances of the rounded
+    centred points within the per-entry bound, every entry <= 0, and the
+    preference the exact off-diagonal median of the S it wrote."""
+    X, _ = synth.workload(1)
+    n, d = X.shape
+    Sd, p = capi.ap_similarity(torch.from_numpy(X).cuda(), precision="bf16")
+    rows = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(9).choice(n, 64, replace=False)]))
+    Srows = Sd[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    Xt = oap.similarity_bf16_inputs(X)
+    Sref = oap.similarity(Xt[rows], Xt)
+    nrm = (Xt ** 2).sum(axis=1)
+    K = (d + 63) // 64 * 64
+    bound = 4.0 * (K + 4) * 2.0 ** -24 * (nrm[rows][:, None] + nrm[None, :]) + 1e-30
+    off = np.ones_like(Srows, dtype=bool)
+    off[np.arange(rows.size), rows] = False
+    assert (np.abs(Srows - Sref)[off] <= bound[off]).all()
+    assert (Srows[off] <= 0).all()
+    assert (Srows[~off] == np.float32(p)).all()
+    S = Sd.cpu().numpy()
+    assert p == np.float32(np.median(S[~np.eye(n, dtype=bool)].astype(np.float64)))
+
+
 def test_bf16_similarity_error_vs_unrounded_points_reported():
     """The bf16 path against the float64 distances of the unrounded points:
     stated, not bounded by float32 rounding (the inputs differ by bf16
