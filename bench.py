@@ -982,6 +982,54 @@ def lap_only(args):
           flush=True)
 
 
+def sweep_configs(args):
+    """Every admissible sweep configuration (cluster 1-16 x float4 per thread
+    x stages) timed at each N of --sweep-configs on random 16-D points (bf16
+    S, damping 0.9, 6 fixed iterations, per-launch CUDA-event time), with the
+    default configuration; one JSON line per N."""
+    import torch
+
+    from paper_0910_1650_gb300 import capi
+
+    peaks, _ = _peaks()
+    for n in args.sweep_configs:
+        torch.manual_seed(0)
+        X = torch.randn(n, 16, device="cuda")
+        S, _ = capi.ap_similarity(X, precision="bf16")
+        R = capi.empty_square(n, "cuda", 0.0)
+        A = capi.empty_square(n, "cuda", 0.0)
+        dflt = capi.ap_sweep_get_config(n)
+        rows = []
+        for cl in range(1, 17):
+            for ept in range(1, 5):
+                for ns in (2, 3, 4):
+                    try:
+                        capi.ap_sweep_set_config(n, cl, ept, ns)
+                    except capi.ApgbError:
+                        continue
+                    cfg = capi.ap_sweep_get_config(n)
+                    R.zero_()
+                    A.zero_()
+                    _, _, r, _ = capi.ap_iterate(S, R, A, damping=0.9, max_iter=6, conv_iter=0,
+                                                 time_sweep=True, decisions=False)
+                    rows.append((r["sweep_ms"] / max(1, r["sweep_launches"]), cl, ept, ns,
+                                 cfg["clusters"] * cl))
+        capi.ap_sweep_set_config(n)
+        rows.sort()
+        frac = lambda ms: round(20.0 * n * n / 1e6 / ms / peaks["hbm_gbs"], 3)
+        key = (dflt["cluster"], dflt["ept"], dflt["stages"])
+        dms = [m for m, c, e, st, _ in rows if (c, e, st) == key]
+        print(json.dumps({"case": "sweep_configs", "n": n,
+                          "default": {"cluster": key[0], "ept": key[1], "stages": key[2],
+                                      "ctas": dflt["clusters"] * key[0],
+                                      "ms": round(dms[0], 3) if dms else None,
+                                      "frac": frac(dms[0]) if dms else None},
+                          "fastest": [{"cluster": c, "ept": e, "stages": st, "ctas": k, "ms": round(m, 3),
+                                       "frac": frac(m)} for m, c, e, st, k in rows[:5]]}), flush=True)
+        del S, R, A
+        torch.cuda.empty_cache()
+
+
 def lap_full_only(args):
     """Algorithm 3 in full (Steps 1-4, the refinement included) on all 1e6
     points of the 1e6-point workload, once, as the time-to-converge section
@@ -1026,6 +1074,9 @@ def main():
     ap.add_argument("--lap-only", type=int, default=0, metavar="N",
                     help="profiling aid: one landmark AP (Steps 1-2, 20000 landmarks, bf16) on the "
                          "first N points of the 1e6-point workload, print one JSON line")
+    ap.add_argument("--sweep-configs", type=int, nargs="+", default=None, metavar="N",
+                    help="profiling aid: time every admissible sweep configuration at each N, "
+                         "one JSON line per N")
     ap.add_argument("--lap-full-only", action="store_true",
                     help="profiling aid: one call of Algorithm 3 Steps 1-4 (refined) on all 1e6 "
                          "points, print one JSON line")
@@ -1047,6 +1098,9 @@ def main():
         return
     if args.lap_full_only:
         lap_full_only(args)
+        return
+    if args.sweep_configs:
+        sweep_configs(args)
         return
     if args.pap_table2:
         import torch

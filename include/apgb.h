@@ -578,7 +578,7 @@ int32_t   ap_shard_finish(const float* S, float* R, float* A, int64_t n, int64_t
  * hold ap_sweep_autotune_workspace_size(n, ld) bytes.  Synchronous.
  * ------------------------------------------------------------------------- */
 typedef struct ap_sweep_config {
-    int32_t cluster;    /* 1, 2, 4, 8 or 16                                      */
+    int32_t cluster;    /* CTAs per cluster, 1 .. 16                             */
     int32_t ept;        /* 1..4                                                  */
     int32_t stages;     /* 2..4                                                  */
     int32_t threads;    /* out: threads per CTA                                  */

@@ -759,8 +759,7 @@ static int32_t max_clusters(int ept, int C, int T, size_t smem, int* out) {
 
 // Validates (C, ept, ns) for n and fills the derived launch parameters.
 static int32_t make_config(int n, int C, int ept, int ns, SweepConfig* c) {
-    if (C < 1 || C > kMaxCluster || (C & (C - 1)) || ept < 1 || ept > 4 || ns < 2 ||
-        ns > kMaxStages)
+    if (C < 1 || C > kMaxCluster || ept < 1 || ept > 4 || ns < 2 || ns > kMaxStages)
         return AP_ERR_INVALID_ARG;
     const int n4 = (n + 3) / 4;
     if (C > 1 && n4 < 8 * C) return AP_ERR_UNSUPPORTED;
@@ -792,14 +791,14 @@ static std::map<int64_t, SweepConfig> g_chosen;         // (device, n) -> defaul
 
 // The default configuration.  Cluster size: the smallest power of two whose
 // slice is at most 640 float4 columns (a stage of at most 30 KB); when even 16
-// CTAs leave a wider slice, every cluster size that admits a configuration
-// competes.  Among the candidates the most resident CTAs (clusters x cluster
-// size) win -- at large n the 16-CTA clusters pack poorly onto the GPCs and
-// idle SMs cost more than anything else -- and ties go to three stages, then
-// four, then two, and to 3, 4, 2, 1 float4 per thread.  (On the 64-D mixtures
-// this picks the fastest measured configuration, or one within 5 % of it, at
-// every n from 4096 to 100000.)  A configuration pinned for n (by
-// ap_sweep_set_config or the autotuner) takes precedence.
+// CTAs leave a wider slice, every cluster size from 1 to 16 that admits a
+// configuration competes (sizes that are not powers of two pack better onto
+// the GPCs: 9-CTA clusters keep 135 SMs busy at 60000 points where 8-CTA ones
+// keep 120).  Among the candidates the most resident CTAs (clusters x cluster
+// size) win -- idle SMs cost more than anything else -- and ties go to three
+// stages, then four, then two, and to 3, 4, 2, 1 float4 per thread.  A
+// configuration pinned for n (by ap_sweep_set_config or the autotuner) takes
+// precedence.
 static int32_t choose_config(int n, SweepConfig* c) {
     {
         std::lock_guard<std::mutex> lock(g_pin_mu);
@@ -825,7 +824,7 @@ static int32_t choose_config(int n, SweepConfig* c) {
     auto ept_rank = [](int e) { return e == 3 ? 3 : e == 4 ? 2 : e == 2 ? 1 : 0; };
     bool found = false;
     SweepConfig best{}, cand{};
-    for (int C = wide ? 1 : C0; C <= (wide ? kMaxCluster : C0); C *= 2)
+    for (int C = wide ? 1 : C0; C <= (wide ? kMaxCluster : C0); C = wide ? C + 1 : 2 * C)
         for (int ns = 2; ns <= kMaxStages; ++ns)
             for (int ept = 1; ept <= 4; ++ept) {
                 if (make_config(n, C, ept, ns, &cand) != AP_OK) continue;
@@ -1608,7 +1607,7 @@ APGB_API int32_t ap_sweep_set_config(int64_t n, const ap_sweep_config* cfg) {
 }
 
 static void for_each_candidate(int n, const std::function<void(const SweepConfig&)>& f) {
-    for (int C = 1; C <= kMaxCluster; C *= 2)
+    for (int C = 1; C <= kMaxCluster; ++C)
         for (int ept = 1; ept <= 4; ++ept)
             for (int ns = 2; ns <= kMaxStages; ++ns) {
                 SweepConfig c;

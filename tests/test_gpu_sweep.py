@@ -82,9 +82,10 @@ def test_sweep_matches_oracle_fixed_iterations(name, lam, iters):
 
 
 def test_every_sweep_configuration_matches_oracle():
-    """Every admissible launch configuration (cluster size x float4 per thread x
-    stages; two stages run rows unpipelined, three or more pipelined across the
-    cluster exchange) against the oracle, on a size with a ragged float4 tail."""
+    """Every admissible launch configuration (cluster size 1-16, powers of two
+    or not, x float4 per thread x stages; two stages run rows unpipelined,
+    three or more pipelined across the cluster exchange) against the oracle,
+    on a size with a ragged float4 tail."""
     S = workload_S("ragged_5003")
     n = S.shape[0]
     Sd = dev_square(S)
@@ -92,7 +93,7 @@ def test_every_sweep_configuration_matches_oracle():
     want_dec = None
     tried = set()
     try:
-        for C in (1, 2, 4, 8, 16):
+        for C in range(1, 17):
             for ept in (1, 2, 3, 4):
                 for ns in (2, 3, 4):
                     try:
@@ -110,7 +111,7 @@ def test_every_sweep_configuration_matches_oracle():
     finally:
         capi.ap_sweep_set_config(n)
     assert {k[2] for k in tried} >= {2, 3, 4}
-    assert {k[0] for k in tried} >= {1, 4, 16}
+    assert {k[0] for k in tried} >= {1, 3, 4, 6, 9, 12, 16}
 
 
 def test_sweep_at_the_bench_size_matches_oracle():
