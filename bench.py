@@ -1025,7 +1025,11 @@ def sweep_configs(args):
                                       "ms": round(dms[0], 3) if dms else None,
                                       "frac": frac(dms[0]) if dms else None},
                           "fastest": [{"cluster": c, "ept": e, "stages": st, "ctas": k, "ms": round(m, 3),
-                                       "frac": frac(m)} for m, c, e, st, k in rows[:5]]}), flush=True)
+                                       "frac": frac(m)} for m, c, e, st, k in rows[:5]],
+                          "fastest_power_of_two": [{"cluster": c, "ept": e, "stages": st, "ctas": k,
+                                                    "ms": round(m, 3), "frac": frac(m)}
+                                                   for m, c, e, st, k in rows if c & (c - 1) == 0][:1]}),
+              flush=True)
         del S, R, A
         torch.cuda.empty_cache()
 
