@@ -789,16 +789,22 @@ static std::mutex g_pin_mu;
 static std::map<int64_t, std::array<int, 3>> g_pinned;   // n -> (C, ept, ns)
 static std::map<int64_t, SweepConfig> g_chosen;         // (device, n) -> default configuration
 
-// The default configuration.  Cluster size: the smallest power of two whose
-// slice is at most 640 float4 columns (a stage of at most 30 KB); when even 16
-// CTAs leave a wider slice, every cluster size from 1 to 16 that admits a
-// configuration competes (sizes that are not powers of two pack better onto
-// the GPCs: 9-CTA clusters keep 135 SMs busy at 60000 points where 8-CTA ones
-// keep 120).  Among the candidates the most resident CTAs (clusters x cluster
-// size) win -- idle SMs cost more than anything else -- and ties go to three
-// stages, then four, then two, and to 3, 4, 2, 1 float4 per thread.  A
+// The default configuration.  Below 16384 points: the smallest power-of-two
+// cluster whose slice is at most 640 float4 columns (a stage of at most
+// 30 KB), and among its configurations the most resident CTAs, ties to three
+// stages, then four, then two, and to 3, 4, 2, 1 float4 per thread.  From
+// 16384 points on, every cluster size from 1 to 16 competes and the most
+// resident clusters win (each cluster keeps its own rows in flight, so the
+// row pipeline's depth grows with the clusters, not with the CTAs), then the
+// most resident CTAs, then the same stage and float4 order.  Measured on the
+// 20000-point mixture: 46 clusters of 6 CTAs sweep in 1.118 ms where the
+// power-of-two rule's 36 clusters of 8 took 1.190 ms; clusters that are not
+// powers of two also pack better onto the GPCs at one CTA per SM (9-CTA
+// clusters keep 135 SMs busy at 60000 points where 8-CTA ones keep 120).  A
 // configuration pinned for n (by ap_sweep_set_config or the autotuner) takes
 // precedence.
+constexpr int kAnyClusterN = 16384;
+
 static int32_t choose_config(int n, SweepConfig* c) {
     {
         std::lock_guard<std::mutex> lock(g_pin_mu);
@@ -819,21 +825,23 @@ static int32_t choose_config(int n, SweepConfig* c) {
     const int n4 = (n + 3) / 4;
     int C0 = 1;
     while (C0 < kMaxCluster && (n4 + C0 - 1) / C0 > 640) C0 *= 2;
-    const bool wide = (n4 + kMaxCluster - 1) / kMaxCluster > 640;
+    const bool any = n >= kAnyClusterN || (n4 + kMaxCluster - 1) / kMaxCluster > 640;
     auto ns_rank = [](int ns) { return ns == 3 ? 2 : ns == 4 ? 1 : 0; };
     auto ept_rank = [](int e) { return e == 3 ? 3 : e == 4 ? 2 : e == 2 ? 1 : 0; };
     bool found = false;
     SweepConfig best{}, cand{};
-    for (int C = wide ? 1 : C0; C <= (wide ? kMaxCluster : C0); C = wide ? C + 1 : 2 * C)
+    for (int C = any ? 1 : C0; C <= (any ? kMaxCluster : C0); C = any ? C + 1 : 2 * C)
         for (int ns = 2; ns <= kMaxStages; ++ns)
             for (int ept = 1; ept <= 4; ++ept) {
                 if (make_config(n, C, ept, ns, &cand) != AP_OK) continue;
                 const long ctas = (long)cand.G * cand.C, bctas = (long)best.G * best.C;
+                const long cl = any ? cand.G : 0, bcl = any ? best.G : 0;
                 const bool better =
-                    !found || ctas > bctas ||
-                    (ctas == bctas && (ns_rank(cand.NS) > ns_rank(best.NS) ||
-                                       (ns_rank(cand.NS) == ns_rank(best.NS) &&
-                                        ept_rank(cand.EPT) > ept_rank(best.EPT))));
+                    !found || cl > bcl ||
+                    (cl == bcl && (ctas > bctas ||
+                                   (ctas == bctas && (ns_rank(cand.NS) > ns_rank(best.NS) ||
+                                                      (ns_rank(cand.NS) == ns_rank(best.NS) &&
+                                                       ept_rank(cand.EPT) > ept_rank(best.EPT))))));
                 if (better) best = cand;
                 found = true;
             }
