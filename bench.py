@@ -596,7 +596,12 @@ def batch_learned(dev, count=256, n_train=32):
     # the batch about 1.5x slower than freshly allocated ones
     torch.cuda.empty_cache()
     sizes, _ = synth.batch_problem_sizes(count)
-    B = batched.Batch(batched.image_batch(count), sizes[:count])
+    # the features are drawn first (a pool of host processes): drawing them
+    # while the timed similarity calls run starved those calls' host-side set-up
+    # and left the GPU waiting (20-46 ms for the same work)
+    problems = list(batched.image_batch(count))
+    B = batched.Batch(problems, sizes[:count])
+    del problems
     peaks, src = _peaks()
     tflops = B.gemm_flops / (B.sim_ms / 1e3) / 1e12
     R = torch.zeros_like(B.S)
