@@ -681,12 +681,23 @@ __global__ void sweep_init_kernel(const SweepArgs* __restrict__ table, int max_i
     }
 }
 
+// NaN/Inf entries of every problem's S.  Rows start 16-byte aligned (S is
+// 16-byte aligned and ld % 4 == 0), so each row is read as float4 up to its
+// last whole group of four, then the ragged tail one float at a time.
 __global__ void nonfinite_kernel(const SweepArgs* __restrict__ table) {
     const SweepArgs& a = table[blockIdx.y];
+    const int n4 = a.n >> 2;
     int local = 0;
-    for (int i = blockIdx.x; i < a.n; i += gridDim.x)
-        for (int k = threadIdx.x; k < a.n; k += blockDim.x)
-            if (!isfinite(a.S[(int64_t)i * a.ld + k])) ++local;
+    for (int i = blockIdx.x; i < a.n; i += gridDim.x) {
+        const float* row = a.S + (int64_t)i * a.ld;
+        const float4* row4 = reinterpret_cast<const float4*>(row);
+#pragma unroll 4
+        for (int k = threadIdx.x; k < n4; k += blockDim.x) {
+            const float4 v = __ldg(row4 + k);
+            local += !isfinite(v.x) + !isfinite(v.y) + !isfinite(v.z) + !isfinite(v.w);
+        }
+        for (int k = 4 * n4 + threadIdx.x; k < a.n; k += blockDim.x) local += !isfinite(row[k]);
+    }
     local = __reduce_add_sync(0xffffffffu, local);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(&a.st->nonfinite, local);
 }

@@ -232,9 +232,15 @@ def test_exemplars_none():
     assert ex["status"] == capi.AP_NO_EXEMPLARS
 
 
-def test_nonfinite_similarity_rejected():
-    S = workload_S("small_37")
-    S[3, 7] = np.nan
+@pytest.mark.parametrize("at,bad", [((3, 7), np.nan), ((36, 36), np.inf), ((0, 33), -np.inf),
+                                    ((20, 36), np.nan)])
+def test_nonfinite_similarity_rejected(at, bad):
+    """37 columns: 9 groups of four read as float4, column 36 the ragged tail;
+    a NaN or Inf anywhere, the diagonal included, is rejected."""
+    X, _ = synth.gaussian_mixture(37, 2, 3, 5, 6.0, 1.0)
+    S = oap.build_similarity(X)[0].astype(np.float32).astype(np.float64)
+    assert S.shape == (37, 37)
+    S[at] = bad
     with pytest.raises(capi.ApgbError) as e:
         capi.ap_iterate(dev_square(S), damping=0.5, max_iter=3, conv_iter=0)
     assert e.value.status == -5
