@@ -1213,7 +1213,12 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     for (int b = 0; b < count; ++b)
         if (hs[b].nonfinite) return AP_ERR_NONFINITE;
 
-    // iterations per host check: about 4 ms of sweeping at full bandwidth
+    // iterations per host check (at most 64): about 25 ms of sweeping at full
+    // bandwidth for one problem -- the stop rule runs on the device, so the
+    // launches of a chunk after convergence do no work, while every check
+    // costs a host round trip and chunks under 4 iterations run without a
+    // graph -- and about 4 ms for a batch, whose work list is rebuilt at a
+    // check once a problem has stopped
     std::vector<char> active(count, 1);
     auto chunk_for = [&]() {
         if (p->check_every > 0) return (int)p->check_every;
@@ -1221,7 +1226,8 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
         for (int b = 0; b < count; ++b)
             if (active[b]) elems += (double)P[b].n * (double)P[b].n;
         const double t_iter = 20.0 * elems / 6.0e12 + 6e-6;
-        return (int)std::min(64.0, std::max(1.0, 4e-3 / t_iter));
+        const double target = count == 1 ? 25e-3 : 4e-3;
+        return (int)std::min(64.0, std::max(1.0, target / t_iter));
     };
     int chunk = chunk_for();
     const int64_t total = (int64_t)p->max_iter + 1;
