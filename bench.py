@@ -189,10 +189,10 @@ def run_gpu(args):
         capi.ap_similarity(X_in, S, precision=args.precision)
         if timed:
             phase_ev[1].record(stream)
-        R.zero_()
-        A.zero_()
+        # a cold start (R = A = 0) without clearing R and A: the library reads zeros
         _, _, res, _ = capi.ap_iterate(S, R, A, damping=DAMPING, max_iter=MAX_ITER,
-                                       conv_iter=CONV_ITER, time_sweep=True, decisions=False)
+                                       conv_iter=CONV_ITER, time_sweep=True, decisions=False,
+                                       cold=True)
         if timed:
             phase_ev[2].record(stream)
         idx, ex = capi.ap_exemplars(S, R, A)

@@ -92,6 +92,11 @@ typedef struct ap_params {
  * ap_iterate and ap_iterate_batched skip their own check, which reads S once
  * more (4 bytes per element, a fifth of one iteration's traffic). */
 #define AP_FLAG_S_CHECKED 8
+/* ap_params.flags, ap_iterate and ap_iterate_batched: a cold start (Eq. 1:
+ * R = A = 0) whatever R and A hold on entry; the caller need not clear them.
+ * The first sweeps read zeros from the workspace instead of R and A, which
+ * are then written as usual. */
+#define AP_FLAG_COLD 16
 
 /* Outputs of Algorithm 1 (Section 2): dpsim = sum of the data-point
  * similarities to their exemplars, expref = sum of the exemplars'

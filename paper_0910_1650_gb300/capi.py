@@ -26,6 +26,7 @@ AP_FLAG_TIME_SWEEP = 1
 AP_FLAG_NO_GRAPH = 2
 AP_FLAG_PAP_CARRY_R = 4
 AP_FLAG_S_CHECKED = 8
+AP_FLAG_COLD = 16
 AP_LANDMARK_UNIFORM, AP_LANDMARK_SCORE, AP_LANDMARK_GIVEN = 0, 1, 2
 AP_ERR_TOO_LARGE = -7
 AP_ERR_CAPACITY = -8
@@ -361,11 +362,13 @@ def ap_preference_median(S, stream=None):
 
 
 def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check_every=0,
-               time_sweep=False, decisions=True, graph=True, s_checked=False, stream=None):
+               time_sweep=False, decisions=True, graph=True, s_checked=False, cold=False,
+               stream=None):
     """Runs Algorithm 1 in place on (R, A) (zeros when omitted).  ``graph``:
     enqueue each chunk of iterations as one CUDA graph (ignored with
     ``time_sweep``); ``s_checked``: S is known finite (skip the library's
-    NaN/Inf pass).  Returns (R, A, result dict, decisions int32 tensor or None)."""
+    NaN/Inf pass); ``cold``: start from R = A = 0 whatever R and A hold (they
+    are not read).  Returns (R, A, result dict, decisions int32 tensor or None)."""
     _dev_f32(S, "S")
     n = S.shape[0]
     if R is None:
@@ -379,7 +382,7 @@ def ap_iterate(S, R=None, A=None, damping=0.5, max_iter=200, conv_iter=15, check
     dec = torch.empty(n, dtype=torch.int32, device=S.device) if decisions else None
     p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every),
                  (AP_FLAG_TIME_SWEEP if time_sweep else 0) | (0 if graph else AP_FLAG_NO_GRAPH)
-                 | (AP_FLAG_S_CHECKED if s_checked else 0))
+                 | (AP_FLAG_S_CHECKED if s_checked else 0) | (AP_FLAG_COLD if cold else 0))
     res = ApResult()
     ws = workspace(lib().ap_iterate_workspace_size(n, S.stride(0)), S.device)
     st = lib().ap_iterate(C.c_void_p(S.data_ptr()), C.c_void_p(R.data_ptr()),
@@ -403,7 +406,7 @@ def ap_iterate_batched_workspace(n, ld, device):
 
 
 def ap_iterate_batched(S, R, A, offsets, n, ld, damping=0.5, max_iter=200, conv_iter=15,
-                       check_every=0, decisions=False, ws=None, stream=None):
+                       check_every=0, decisions=False, ws=None, cold=False, stream=None):
     """Algorithm 1 on several problems stored in 1-D float32 arenas (CUDA
     tensors).  Problem b: n[b] x n[b] at element offset offsets[b], leading
     dimension ld[b].  Returns (list of result dicts, decisions or None)."""
@@ -413,7 +416,8 @@ def ap_iterate_batched(S, R, A, offsets, n, ld, damping=0.5, max_iter=200, conv_
     count = len(n)
     off_a, n_a, ld_a = _i64_array(offsets), _i64_array(n), _i64_array(ld)
     dec = torch.empty(sum(int(x) for x in n), dtype=torch.int32, device=S.device) if decisions else None
-    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every), 0)
+    p = ApParams(float(damping), int(max_iter), int(conv_iter), int(check_every),
+                 AP_FLAG_COLD if cold else 0)
     out = (ApResult * count)()
     if ws is None:
         ws = ap_iterate_batched_workspace(n, ld, S.device)

@@ -87,6 +87,7 @@ struct SweepArgs {
     int32_t*     eflag;    // exemplar flags of the previous decisions
     int32_t*     dec;      // decisions (may be null)
     SweepState*  st;
+    const float* zero;     // cold start: zeros read as R_0 (t = 1) and A_0 (t <= 2); else null
 };
 
 // One unit of a launch's work list: rows first, first + stride, ... (count
@@ -250,9 +251,13 @@ sweep_kernel(SweepLaunch L) {
                     ptx::mbar_arrive_expect_tx(&ctl->full[s], row_bytes);
                     if (v.nslice > 0) {
                         const int64_t off = (int64_t)(v.first + r * v.stride) * a.ld + 4 * (int64_t)v.f_begin;
+                        // cold start: R_0 and A_0 are zeros, read from a small zeroed
+                        // buffer (it stays in L2) instead of the caller's R and A
+                        const float* rsrc = (a.zero && v.t == 1) ? a.zero : v.Rin + off;
+                        const float* asrc = (a.zero && v.t <= 2) ? a.zero : a.A + off;
                         if (v.doR) ptx::bulk_g2s(sS(s), a.S + off, slice_bytes, &ctl->full[s]);
-                        ptx::bulk_g2s(sR(s), v.Rin + off, slice_bytes, &ctl->full[s]);
-                        ptx::bulk_g2s(sA(s), a.A + off, slice_bytes, &ctl->full[s]);
+                        ptx::bulk_g2s(sR(s), rsrc, slice_bytes, &ctl->full[s]);
+                        ptx::bulk_g2s(sA(s), asrc, slice_bytes, &ctl->full[s]);
                     }
                     issued = r + 1;
                 };
@@ -1018,6 +1023,8 @@ struct SweepWs {
     int* ubeg;
     float* pool;                  // per-unit column partials, nmax floats each
     SweepState* states;           // one per problem, contiguous (one read-back per check)
+    float* zero;                  // cold start: zeros, the widest problem's slice
+    size_t zero_bytes;
     std::vector<SweepArgs> host;
 };
 
@@ -1031,12 +1038,18 @@ static size_t carve_sweep(void* ws, const Problem* P, int count, const Plan& pla
     int* ubeg = cv.take<int>((size_t)std::max(plan.c.R, 1) + 1);
     float* pool = cv.take<float>(max_units(count, plan.c) * (size_t)plan.nmax);
     SweepState* states = cv.take<SweepState>((size_t)count);
+    int64_t w4max = 1;
+    for (int b = 0; b < count; ++b)
+        w4max = std::max<int64_t>(w4max, ((P[b].n + 3) / 4 + plan.c.C - 1) / plan.c.C);
+    float* zero = cv.take<float>((size_t)w4max * 4);
     if (w) {
         w->table = table;
         w->units = units;
         w->ubeg = ubeg;
         w->pool = pool;
         w->states = states;
+        w->zero = zero;
+        w->zero_bytes = (size_t)w4max * 16;
         w->host.assign(count, SweepArgs{});
     }
     for (int b = 0; b < count; ++b) {
@@ -1179,6 +1192,12 @@ static int32_t run_batch(const Problem* P, int count, const ap_params* p, ap_res
     carve_sweep(ws, P, count, plan, &w);
     const SweepConfig& c = plan.c;
     for (auto& a : w.host) a.lam = p->damping;
+    if (p->flags & AP_FLAG_COLD) {
+        // R and A start at zero whatever the buffers hold: the first launches
+        // read this zeroed buffer instead
+        AP_CUDA_TRY(cudaMemsetAsync(w.zero, 0, w.zero_bytes, s));
+        for (auto& a : w.host) a.zero = w.zero;
+    }
     // the problem table and the work list in force (re-planned as problems finish)
     Plan cur = plan;
     auto upload = [&]() -> int32_t {

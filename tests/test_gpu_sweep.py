@@ -232,6 +232,52 @@ def test_exemplars_none():
     assert ex["status"] == capi.AP_NO_EXEMPLARS
 
 
+@pytest.mark.parametrize("iters,conv", [(1, 0), (2, 0), (30, 0), (1000, 15)])
+def test_cold_start_reads_neither_r_nor_a(iters, conv):
+    """AP_FLAG_COLD: with R and A full of NaN on entry the run equals, bit for
+    bit, the run from zeroed R and A (the first launch reads zeros for R_0 and
+    A_0, the second for A_0), for fixed iterations and to convergence."""
+    S = workload_S("ragged_5003")
+    n = S.shape[0]
+    Sd = dev_square(S)
+    R0 = capi.empty_square(n, "cuda", 0.0)
+    A0 = capi.empty_square(n, "cuda", 0.0)
+    R0, A0, r0, d0 = capi.ap_iterate(Sd, R0, A0, damping=0.9, max_iter=iters, conv_iter=conv)
+    Rn = capi.empty_square(n, "cuda", float("nan"))
+    An = capi.empty_square(n, "cuda", float("nan"))
+    Rn, An, rn, dn = capi.ap_iterate(Sd, Rn, An, damping=0.9, max_iter=iters, conv_iter=conv, cold=True)
+    assert rn["iters"] == r0["iters"] and rn["converged"] == r0["converged"]
+    assert torch.equal(Rn, R0) and torch.equal(An, A0) and torch.equal(dn, d0)
+
+
+def test_cold_start_batched():
+    """The same flag on a batch of three problems of different sizes."""
+    sizes = [37, 300, 1001]
+    mats = [oap.build_similarity(synth.gaussian_mixture(m, 4, 3, 60 + m, 5.0, 1.0)[0])[0] for m in sizes]
+    ld = [capi.padded_ld(m) for m in sizes]
+    off, at = [], 0
+    for m, l in zip(sizes, ld):
+        off.append(at)
+        at += m * l
+    arena = np.zeros(at, dtype=np.float32)
+    for M, o, l in zip(mats, off, ld):
+        arena[o:o + M.shape[0] * l].reshape(M.shape[0], l)[:, :M.shape[0]] = M
+    Sa = torch.from_numpy(arena).cuda()
+    out = []
+    for cold, fill in ((False, 0.0), (True, float("nan"))):
+        Ra = torch.full_like(Sa, fill)
+        Aa = torch.full_like(Sa, fill)
+        res, _ = capi.ap_iterate_batched(Sa, Ra, Aa, off, sizes, ld, damping=0.9, max_iter=12,
+                                         conv_iter=0, cold=cold)
+        out.append((Ra, Aa, [r["iters"] for r in res]))
+    assert out[0][2] == out[1][2]
+    for m, o, l in zip(sizes, off, ld):                # each problem's n x n (padding is untouched)
+        for k in (0, 1):
+            got = out[1][k][o:o + m * l].view(m, l)[:, :m]
+            want = out[0][k][o:o + m * l].view(m, l)[:, :m]
+            assert torch.equal(got, want)
+
+
 @pytest.mark.parametrize("at,bad", [((3, 7), np.nan), ((36, 36), np.inf), ((0, 33), -np.inf),
                                     ((20, 36), np.nan)])
 def test_nonfinite_similarity_rejected(at, bad):
