@@ -23,16 +23,20 @@ def _data(n=3000, d=16, k=12, seed=31):
     return X
 
 
-@pytest.mark.parametrize("n,L,seed", [(1000, 100, 5), (3001, 600, 99), (50000, 20000, 7)])
+@pytest.mark.parametrize("n,L,seed", [(1000, 100, 5), (3001, 600, 99), (50000, 20000, 7),
+                                      (600000, 20000, 13)])
 def test_uniform_landmarks_exact(n, L, seed):
+    """600000 points: the compaction's 256 blocks take several passes each."""
     X = _data(n, 4, 3, 1)
     idx, lm, res = capi.lap_run(torch.from_numpy(X).cuda(), L, "uniform", seed=seed,
                                 damping=0.9, max_iter=3, conv_iter=0)
     assert np.array_equal(lm.cpu().numpy().astype(np.int64), olap.uniform_landmarks(n, L, seed))
 
 
-def test_score_landmarks_exact():
-    n, L = 2000, 300
+@pytest.mark.parametrize("n,L", [(2000, 300), (400000, 5000)])
+def test_score_landmarks_exact(n, L):
+    """Ties of the score are broken by the lower index, also across the
+    compaction's blocks (400000 points: 256 blocks of several passes)."""
     X = _data(n, 4, 3, 2)
     g = np.random.default_rng(0)
     score = np.round(g.normal(size=n), 2).astype(np.float32)     # many ties
@@ -83,14 +87,17 @@ def _check_assignment(X, E_pts, labels, best=None):
 
 @pytest.mark.parametrize("c_case,n,c,seed", [("mix128", 8000, 700, 1), ("mix128", 3001, 257, 2),
                                            ("mix128", 513, 256, 3), ("mix128", 1000, 1, 4),
-                                           ("subspace100", 5000, 600, 5)])
+                                           ("subspace100", 5000, 600, 5), ("mix300", 3000, 500, 6)])
 def test_lap_assign_full_shape(c_case, n, c, seed):
     """The assignment GEMM's arg-max mode through its own entry (Algorithm 3
     Step 2) at the shapes of the 1e6-point workload: d = 128 (two K blocks)
-    or d = 100 (zero-padded K), up to three 256-column tiles of centres
-    merged by the running arg-max, and dozens of 128-row blocks."""
+    or d = 100 (zero-padded K), and d = 300 (five K blocks), up to three
+    256-column tiles of centres merged by the running arg-max, and dozens of
+    128-row blocks."""
     if c_case == "mix128":
         X, _ = synth.workload(3, scale=n / 1_000_000)
+    elif c_case == "mix300":                                  # K = 320: five K blocks
+        X, _ = synth.gaussian_mixture(n, 300, 20, 41, 4.0, 1.0)
     else:
         X, _ = synth.workload(2, scale=n / 60000)
     X = np.ascontiguousarray(X[:n])
