@@ -617,11 +617,23 @@ sweep_kernel(SweepLaunch L) {
 }
 
 // Column sums in a fixed order, then the stop rule (block 0 of each
-// problem).  Block: 32 columns x 8 lanes over the problem's G unit partials;
-// each lane sums every 8th partial, then the 8 lane sums are added in a fixed
-// tree, so the result does not depend on the schedule.
+// problem).  Block: 32 columns x 16 lanes over the problem's G unit partials;
+// each lane sums every 16th partial, then the 16 lane sums are added in a
+// fixed tree, so the result does not depend on the schedule.
 // Grid: (ceil(n/32), problems).
-constexpr int kFinCols = 32, kFinLanes = 8;
+constexpr int kFinCols = 32, kFinLanes = 32;
+
+// The kFinLanes lane sums of a column added in a fixed pairwise tree.
+__device__ __forceinline__ float lane_tree(const float (*part)[kFinCols], int cx) {
+    float v[kFinLanes];
+#pragma unroll
+    for (int l = 0; l < kFinLanes; ++l) v[l] = part[l][cx];
+#pragma unroll
+    for (int w = kFinLanes / 2; w >= 1; w >>= 1)
+#pragma unroll
+        for (int e = 0; e < w; ++e) v[e] = v[2 * e] + v[2 * e + 1];
+    return v[0];
+}
 
 // Step 4 of Algorithm 1 after launch t (one thread): the exemplar set of
 // iteration t-1 extends or resets the run of unchanged sets; stop once it
@@ -665,8 +677,7 @@ __global__ void __launch_bounds__(kFinCols * kFinLanes) finalize_kernel(const Sw
     part[gy][cx] = s;
     __syncthreads();
     if (gy == 0 && k < a.n) {
-        const float t = ((part[0][cx] + part[1][cx]) + (part[2][cx] + part[3][cx])) +
-                        ((part[4][cx] + part[5][cx]) + (part[6][cx] + part[7][cx]));
+        const float t = lane_tree(part, cx);
         const_cast<float*>(a.colp)[k] = t;
         const_cast<float*>(a.cvec)[k] = a.rkk[k] + t;
     }
@@ -1740,8 +1751,7 @@ __global__ void __launch_bounds__(kFinCols * kFinLanes) shard_reduce_kernel(cons
     part[gy][cx] = s;
     __syncthreads();
     if (gy == 0 && k < a.n) {
-        red[k] = ((part[0][cx] + part[1][cx]) + (part[2][cx] + part[3][cx])) +
-                 ((part[4][cx] + part[5][cx]) + (part[6][cx] + part[7][cx]));
+        red[k] = lane_tree(part, cx);
         red[a.n + k] = a.rkk[k];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
